@@ -1,0 +1,92 @@
+"""Pins of the oracle's circulant preconditioners (Eq. (3.7)) and its dense PCGS."""
+import numpy as np
+import pytest
+from scipy.linalg import toeplitz
+
+import oracle as O
+import tsfcde_workloads as W
+
+
+def _rand_toeplitz(n, seed):
+    rng = np.random.default_rng(seed)
+    col, row = rng.standard_normal(n), rng.standard_normal(n)
+    row[0] = col[0]
+    return toeplitz(col, row)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_circulant_fixed_points(n):
+    c = np.random.default_rng(n).standard_normal(n)
+    C = O.circulant_from_column(c)
+    np.testing.assert_allclose(O.strang_column(C), c)
+    np.testing.assert_allclose(O.tchan_column(C), c)
+
+
+def test_strang_copies_central_diagonals():
+    T = _rand_toeplitz(7, 3)
+    t = O.toeplitz_diagonals(T)
+    c = O.strang_column(T)
+    np.testing.assert_array_equal(c, [t[0], t[1], t[2], t[3], t[-3], t[-2], t[-1]])
+
+
+@pytest.mark.parametrize("n", [4, 7])
+def test_tchan_is_frobenius_optimal(n):
+    """T. Chan's circulant minimises ||C - T||_F over circulants: least squares in the basis of
+    the n cyclic shift matrices."""
+    T = _rand_toeplitz(n, n)
+    basis = [O.circulant_from_column(np.eye(n)[k]) for k in range(n)]
+    Amat = np.stack([b.ravel() for b in basis], axis=1)
+    coef = np.linalg.lstsq(Amat, T.ravel(), rcond=None)[0]
+    np.testing.assert_allclose(O.tchan_column(T), coef, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["strang", "tchan"])
+def test_preconditioner_is_circulant_approx_of_A(kind):
+    """Eq. (3.7) applies s(.) to Q, W, W^T term by term; s is linear, so P = s(A)."""
+    p = W.config_small(n=21, M=8, preconditioner=kind)
+    A, _ = O.level_matrices(p, 2)
+    col = O.strang_column if kind == "strang" else O.tchan_column
+    np.testing.assert_allclose(O.preconditioner_matrix(p, 2), O.circulant_from_column(col(A)),
+                               rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["strang", "tchan"])
+def test_preconditioner_nonsingular(kind):
+    """Theorem 4: Re(Lambda_P) > 0."""
+    p = W.config_small(n=63, M=16, preconditioner=kind)
+    P = O.preconditioner_matrix(p, 0)
+    lam = np.linalg.eigvals(P)
+    assert np.min(lam.real) > 0
+
+
+def _level_rhs(p, lv, j):
+    import math
+    A, B = O.level_matrices(p, j)
+    sigma = 1 - p.alpha / 2
+    g = B @ lv[j] + p.f(p.grid(), (j + sigma) * p.tau)
+    c = O.c_coeffs(p.alpha, j)
+    hist = sum(c[j - s] * (lv[s + 1] - lv[s]) for s in range(j)) if j else 0.0
+    return A, g - p.tau ** (-p.alpha) / math.gamma(2 - p.alpha) * hist
+
+
+@pytest.mark.parametrize("maker,beta,j", [(W.example1, 1.8, 0), (W.example1, 1.8, 1),
+                                          (W.example1, 1.8, 40), (W.example2, 1.5, 64),
+                                          (W.example2, 1.5, 127)])
+def test_pcgs_iterations_in_paper_range(maker, beta, j):
+    """Section 3.2 / Figs. 1-4: Strang-preconditioned CGS needs 6-10 iterations at N = M = 128,
+    alpha = 0.9 (Example 2's first levels have d+- ~ sin t ~ 0 and need fewer); the solution
+    equals the GE solution."""
+    p = maker(127, 128, 0.9, beta)
+    lv = O.run(p, levels=j + 1)
+    A, g = _level_rhs(p, lv, j)
+    sol, its, _ = O.pcgs(A, g, O.preconditioner_matrix(p, j, "strang"))
+    assert 6 <= its <= 10, its
+    np.testing.assert_allclose(sol, lv[j + 1], rtol=1e-10, atol=1e-13)
+
+
+def test_pcgs_without_preconditioner_is_slow():
+    p = W.example1(127, 128, 0.9, 1.8)
+    A, B = O.level_matrices(p, 0)
+    g = B @ p.phi(p.grid())
+    _, its, _ = O.pcgs(A, g, None, maxit=60)
+    assert its == 60

@@ -1,0 +1,219 @@
+"""Pins of the oracle's level solve and time march against the paper and the mathematics."""
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle as O
+import tsfcde_workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.txt")
+
+
+def _rows():
+    out = []
+    for line in open(GOLDEN):
+        line = line.split("#")[0].split()
+        if line:
+            ex, a, b, hi, e2, em = line
+            out.append((ex, float(a), float(b), int(hi), float(e2), float(em)))
+    return out
+
+
+@pytest.mark.parametrize("row", _rows(), ids=lambda r: f"{r[0]}-a{r[1]}-h{r[3]}")
+def test_paper_error_tables(row):
+    """Tables 1 and 7 (Section 4): max_n ||E^n||_0 and max|E| at tau = h."""
+    ex, alpha, beta, hinv, e2_ref, em_ref = row
+    make = W.example1 if ex == "ex1" else W.example2
+    p = make(hinv - 1, hinv, alpha, beta)
+    e2, em = O.errors_vs_exact(p, O.run(p))
+    tol = 0.005 if ex == "ex1" else 0.03
+    assert abs(e2 / e2_ref - 1) < tol, (e2, e2_ref)
+    assert abs(em / em_ref - 1) < tol, (em, em_ref)
+
+
+def test_history_sign_reading():
+    """Eq. (3.1) subtracts the history sum; adding it (Eq. (3.3) as printed) breaks Table 1."""
+    p = W.example1(31, 32, 0.1)
+    e_ok = O.errors_vs_exact(p, O.run(p))[0]
+    # re-run with the history added: negate the scale by flipping through a wrapped source
+    n, x = p.n, p.grid()
+    sigma, tau = 1 - p.alpha / 2, p.tau
+    hs = tau ** (-p.alpha) / math.gamma(2 - p.alpha)
+    Q, Wm = O.matrix_Q(n), O.matrix_W(p.beta, n)
+    u = [p.phi(x)]
+    for j in range(p.M):
+        A, B = O.level_matrices(p, j, Q, Wm)
+        g = B @ u[j] + p.f(x, (j + sigma) * tau)
+        if j >= 1:
+            c = O.c_coeffs(p.alpha, j)
+            g = g + hs * sum(c[j - s] * (u[s + 1] - u[s]) for s in range(j))
+        u.append(np.linalg.solve(A, g))
+    e_bad = O.errors_vs_exact(p, u)[0]
+    assert abs(e_ok / 2.7954e-4 - 1) < 0.005 and e_bad > 10 * e_ok
+
+
+def test_matrix_form_equals_pointwise_scheme():
+    """Eq. (3.3)'s A and B equal the pointwise operator delta_h^beta of Eq. (2.1)
+    (central convection + two-sided shifted sums, u_0 = u_N = 0) applied to unit vectors."""
+    p = W.example2(9, 10, 0.4, 1.45)
+    n, h = p.n, p.h
+    sigma = 1 - p.alpha / 2
+    wgt = O.wsgd_weights(p.beta, n + 2)
+    for j in (0, 3):
+        t = (j + sigma) * p.tau
+        e = O.eta(p.alpha, p.tau, j)
+        gm, Dp, Dm = p.gamma(t), p.d_plus(t), p.d_minus(t)
+
+        def delta(v):  # v holds u_0..u_{n+1} (paper index i = 0..N)
+            out = np.zeros(n)
+            for i in range(1, n + 1):
+                s = gm * (v[i + 1] - v[i - 1]) / (2 * h)
+                s += Dp / h ** p.beta * sum(wgt[k] * v[i - k + 1] for k in range(0, i + 2))
+                s += Dm / h ** p.beta * sum(wgt[k] * v[i + k - 1] for k in range(0, n + 1 - i + 2))
+                out[i - 1] = s
+            return out
+
+        Lm = np.zeros((n, n))
+        for c in range(n):
+            v = np.zeros(n + 2)
+            v[c + 1] = 1.0
+            Lm[:, c] = delta(v)
+        A, B = O.level_matrices(p, j)
+        np.testing.assert_allclose(A, e * np.eye(n) - sigma * Lm, rtol=1e-13, atol=1e-9)
+        np.testing.assert_allclose(B, e * np.eye(n) + (1 - sigma) * Lm, rtol=1e-13, atol=1e-9)
+
+
+def test_matrix_display_small():
+    """Q and W_beta written out for n = 4 as displayed in Eq. (3.2)."""
+    beta = 1.6
+    w = O.wsgd_weights(beta, 5)
+    Wref = np.array([[w[1], w[0], 0, 0],
+                     [w[2], w[1], w[0], 0],
+                     [w[3], w[2], w[1], w[0]],
+                     [w[4], w[3], w[2], w[1]]])
+    np.testing.assert_array_equal(O.matrix_W(beta, 4), Wref)
+    Qref = np.array([[0, 1, 0, 0], [-1, 0, 1, 0], [0, -1, 0, 1], [0, 0, -1, 0]], dtype=float)
+    np.testing.assert_array_equal(O.matrix_Q(4), Qref)
+
+
+def test_crank_nicolson_limit():
+    """alpha = 1, beta = 2: the scheme is Crank-Nicolson for u_t = g u_x + (d+ + d-) u_xx + f."""
+    p = W.example2(23, 16, 1.0, 2.0)
+    lv = O.run(p)
+    n, h, tau, x = p.n, p.h, p.tau, p.grid()
+    D1 = (np.eye(n, k=1) - np.eye(n, k=-1)) / (2 * h)
+    D2 = (np.eye(n, k=1) - 2 * np.eye(n) + np.eye(n, k=-1)) / h ** 2
+    u = p.phi(x)
+    for j in range(p.M):
+        t = (j + 0.5) * tau
+        Lm = p.gamma(t) * D1 + (p.d_plus(t) + p.d_minus(t)) * D2
+        u = np.linalg.solve(np.eye(n) / tau - 0.5 * Lm,
+                            (np.eye(n) / tau + 0.5 * Lm) @ u + p.f(x, t))
+        np.testing.assert_allclose(lv[j + 1], u, rtol=1e-11, atol=1e-13)
+
+
+def test_single_mode_scalar_recurrence():
+    """gamma = 0, beta = 2, phi = sin(pi x), f = 0: every level is c_j sin(pi x_i), where c_j
+    obeys the scalar L2-1_sigma recurrence with the eigenvalue mu = -4 sin^2(pi h/2)/h^2."""
+    alpha, n, M = 0.6, 31, 20
+    p = W.Problem(0.0, 1.0, 1.0, n, M, alpha, 2.0, lambda t: 0.0, lambda t: 0.7,
+                  lambda t: 0.3, lambda x: np.sin(np.pi * x), None)
+    lv = O.run(p)
+    h, tau, sigma = p.h, p.tau, 1 - alpha / 2
+    mu = -4 * math.sin(math.pi * h / 2) ** 2 / h ** 2 * 1.0
+    k = tau ** (-alpha) / math.gamma(2 - alpha)
+    amp = [1.0]
+    for j in range(M):
+        c = O.c_coeffs(alpha, j)
+        hist = sum(c[j - s] * (amp[s + 1] - amp[s]) for s in range(j))
+        # k c_0 (a' - a_j) + k hist = mu (sigma a' + (1-sigma) a_j)
+        a_new = (k * c[0] * amp[j] - k * hist + mu * (1 - sigma) * amp[j]) / (k * c[0] - mu * sigma)
+        amp.append(a_new)
+    x = p.grid()
+    for j in range(M + 1):
+        np.testing.assert_allclose(lv[j], amp[j] * np.sin(np.pi * x), rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("maker,alpha,beta", [(W.config_small, 0.6, 1.7), (W.example2, 0.5, 1.5)])
+def test_second_order_in_h_and_tau(maker, alpha, beta):
+    """Theorem 3: error O(tau^2 + h^2) against the manufactured solution (tau = h)."""
+    errs = []
+    for m in (16, 32, 64):
+        p = maker(m - 1, m, alpha, beta) if maker is W.example2 else maker(n=m - 1, M=m)
+        errs.append(O.errors_vs_exact(p, O.run(p))[0])
+    cos = [O.convergence_order(errs[i], errs[i + 1], 2.0, 1.0) for i in range(2)]
+    assert all(1.8 < c < 2.3 for c in cos), cos
+
+
+def test_gaussian_elimination_vs_mpmath():
+    """Brute force: tiny n, the whole march redone in 40-digit arithmetic from the pointwise
+    scheme (mpmath LU)."""
+    mpmath.mp.dps = 40
+    p = W.example2(5, 4, 0.7, 1.35)
+    lv = O.run(p)
+    n = p.n
+    a = mpmath.mpf(p.alpha)
+    beta = mpmath.mpf(p.beta)
+    sigma = 1 - a / 2
+    tau = mpmath.mpf(1) / p.M
+    h = mpmath.mpf(1) / (n + 1)
+    g = [mpmath.mpf(1)]
+    for k in range(1, n + 3):
+        g.append((1 - (beta + 1) / k) * g[-1])
+    l1, l0, lm = (beta ** 2 + 3 * beta + 2) / 12, (4 - beta ** 2) / 6, (beta ** 2 - 3 * beta + 2) / 12
+    w = [l1 * g[0], l1 * g[1] + l0 * g[0]] + [l1 * g[k] + l0 * g[k - 1] + lm * g[k - 2]
+                                              for k in range(2, n + 2)]
+
+    def aa(l):
+        return (l + sigma) ** (1 - a) - (l - 1 + sigma) ** (1 - a) if l else sigma ** (1 - a)
+
+    def bb(l):
+        return (((l + sigma) ** (2 - a) - (l - 1 + sigma) ** (2 - a)) / (2 - a)
+                - ((l + sigma) ** (1 - a) + (l - 1 + sigma) ** (1 - a)) / 2)
+
+    def cc(j, m):
+        if j == 0:
+            return aa(0)
+        if m == 0:
+            return aa(0) + bb(1)
+        if m == j:
+            return aa(j) - bb(j)
+        return aa(m) + bb(m + 1) - bb(m)
+
+    K = tau ** (-a) / mpmath.gamma(2 - a)
+    xs = [h * (i + 1) for i in range(n)]
+    u = [[mpmath.mpf(float(v)) for v in p.phi(np.array([float(xx) for xx in xs]))]]
+    for j in range(p.M):
+        t = (j + sigma) * tau
+        gm, Dp, Dm = (mpmath.mpf(p.gamma(float(t))), mpmath.mpf(p.d_plus(float(t))),
+                      mpmath.mpf(p.d_minus(float(t))))
+        Lm = mpmath.matrix(n, n)
+        for i in range(n):
+            for c in range(n):
+                v = 0
+                if c == i + 1:
+                    v += gm / (2 * h)
+                if c == i - 1:
+                    v -= gm / (2 * h)
+                if i - c + 1 >= 0:
+                    v += Dp / h ** beta * w[i - c + 1]
+                if c - i + 1 >= 0:
+                    v += Dm / h ** beta * w[c - i + 1]
+                Lm[i, c] = v
+        e = K * cc(j, 0)
+        A = e * mpmath.eye(n) - sigma * Lm
+        B = e * mpmath.eye(n) + (1 - sigma) * Lm
+        uj = mpmath.matrix(u[j])
+        fvals = p.f(np.array([float(xx) for xx in xs]), float(t))
+        rhs = B * uj
+        for i in range(n):
+            hsum = sum(cc(j, j - s) * (u[s + 1][i] - u[s][i]) for s in range(j))
+            rhs[i] += -K * hsum + mpmath.mpf(fvals[i])
+        sol = mpmath.lu_solve(A, rhs)
+        u.append([sol[i] for i in range(n)])
+    for j in range(p.M + 1):
+        ref = np.array([float(v) for v in u[j]])
+        np.testing.assert_allclose(lv[j], ref, rtol=1e-12, atol=1e-15)
