@@ -261,8 +261,13 @@ def tchan_column(T: np.ndarray) -> np.ndarray:
 
 
 def preconditioner_matrix(prob, j: int, kind: Optional[str] = None) -> np.ndarray:
-    """P^{(j+sigma)} of Eq. (3.7): the circulant approximation applied term by term,
-    eta I - sigma (q s(Q) + kappa_+ s(W) + kappa_- s(W^T)); s is linear, so this equals s(A)."""
+    """P^{(j+sigma)} of Eq. (3.7): eta I - sigma (q s(Q) + kappa_+ s(W) + kappa_- s(W^T)).
+
+    The term for W^T is taken as s(W)^T, whose eigenvalues are the conjugates of those of s(W):
+    the diagonalisation that follows Eq. (3.7) writes s(W^T) = F* conj(Lambda_beta) F.  For odd n
+    (and for T. Chan's circulant at any n) s(W)^T equals the circulant approximation of W^T
+    itself; for even n Strang's choice of the middle diagonal makes them differ, and the
+    paper's eigenvalue formula is followed."""
     kind = kind or prob.preconditioner
     n = prob.n
     sigma = 1.0 - prob.alpha / 2.0
@@ -271,8 +276,7 @@ def preconditioner_matrix(prob, j: int, kind: Optional[str] = None) -> np.ndarra
     Q, W = matrix_Q(n), matrix_W(prob.beta, n)
     sQ = circulant_from_column(col(Q))
     sW = circulant_from_column(col(W))
-    sWT = circulant_from_column(col(W.T))
-    return e * np.eye(n) - sigma * (q * sQ + kp * sW + km * sWT)
+    return e * np.eye(n) - sigma * (q * sQ + kp * sW + km * sW.T)
 
 
 def pcgs(A: np.ndarray, b: np.ndarray, P: Optional[np.ndarray], tol: float = 1e-12,

@@ -51,6 +51,23 @@ def test_preconditioner_is_circulant_approx_of_A(kind):
 
 
 @pytest.mark.parametrize("kind", ["strang", "tchan"])
+@pytest.mark.parametrize("n", [5, 8, 21])
+def test_transpose_term_reading(kind, n):
+    """s(W)^T (used for the W^T term, as the conj(Lambda_beta) of the diagonalisation after
+    Eq. (3.7) states) equals the circulant approximation of W^T for odd n and for T. Chan;
+    its eigenvalues are the conjugates of those of s(W)."""
+    W_ = O.matrix_W(1.6, n)
+    col = O.strang_column if kind == "strang" else O.tchan_column
+    sW = O.circulant_from_column(col(W_))
+    direct = O.circulant_from_column(col(W_.T))
+    if n % 2 == 1 or kind == "tchan":
+        np.testing.assert_allclose(sW.T, direct, atol=1e-15)
+    lam = np.fft.fft(col(W_))
+    lamT = np.fft.fft(sW.T[:, 0])
+    np.testing.assert_allclose(lamT, np.conj(lam), atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["strang", "tchan"])
 def test_preconditioner_nonsingular(kind):
     """Theorem 4: Re(Lambda_P) > 0."""
     p = W.config_small(n=63, M=16, preconditioner=kind)
