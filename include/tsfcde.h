@@ -1,0 +1,159 @@
+/*
+ * tsfcde.h -- C ABI of the GB300 solver for the time-space fractional convection-diffusion
+ * equation (TSFCDE) of Gu, Huang, Ji, Carpentieri and Alikhanov (arXiv:1603.00279).
+ *
+ * Problem (Eq. (1.1)): Caputo d^alpha_t u = gamma(t) u_x + d_+(t) aD^beta_x u + d_-(t) xD^beta_b u
+ * + f(x,t) on [a,b] x (0,T], u(x,0) = phi(x), u(a,t) = u(b,t) = 0, alpha in (0,1], beta in (1,2],
+ * d_+- >= 0.
+ *
+ * Method: the implicit difference scheme Eq. (2.1) (L2-1_sigma in time, Lemma 1; two-sided
+ * weighted-shifted Grunwald operators in space, Lemma 2), written per level as the nonsymmetric
+ * Toeplitz system Eq. (3.3), A^{(j+sigma)} u^{j+1} = B^{(j+sigma)} u^j - history + f^{j+sigma}
+ * (the history term is subtracted, as in Eq. (3.1)), and solved level by level as in Algorithm
+ * "Practical implementation of IDS": the right-hand side is assembled with an FFT Toeplitz
+ * product and the system is solved with CGS preconditioned by the circulant P^{(j+sigma)} of
+ * Eq. (3.7).
+ *
+ * Conventions shared by every entry point:
+ *   - N is the number of INTERIOR grid points (the paper's N-1): h = (b-a)/(N+1),
+ *     x_i = a + i h for i = 1..N; tau = T/M, sigma = 1 - alpha/2.
+ *   - Vectors passed in or out hold the N interior values in natural order, float64, in HOST
+ *     memory unless an argument says otherwise.  The caller owns every buffer it passes; the
+ *     library owns all device memory it allocates and frees it in tsfcde_free().
+ *   - Every call returns a status (TSFCDE_OK = 0 or one of the TSFCDE_E_* codes below);
+ *     tsfcde_strerror() turns it into text.  A context stays valid after E_NOT_CONVERGED; after
+ *     any other error it may only be freed.
+ *   - Calls on one context must not overlap; different contexts are independent.
+ *   - All device work runs on CUDA device 0 of the calling process unless `device` in the
+ *     options says otherwise.
+ */
+#ifndef TSFCDE_H
+#define TSFCDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------------- */
+#define TSFCDE_OK 0
+#define TSFCDE_E_INVALID_ARG 1      /* an argument is out of the ranges of Eq. (1.1) or NULL     */
+#define TSFCDE_E_NOMEM 2            /* device or host allocation failed                          */
+#define TSFCDE_E_CUDA 3             /* a CUDA runtime call failed                                */
+#define TSFCDE_E_NONFINITE 4        /* a callback or an iterate produced NaN/Inf                 */
+#define TSFCDE_E_NOT_CONVERGED 5    /* CGS reached maxit on some level (state stays valid)       */
+#define TSFCDE_E_BREAKDOWN 6        /* CGS breakdown: rho = 0 or (r~, A p^) = 0                  */
+#define TSFCDE_E_SINGULAR_PRECOND 7 /* an eigenvalue of the circulant P vanished (Theorem 4)      */
+#define TSFCDE_E_TIMEOUT 8          /* a device-wide barrier wait ran out of its bound            */
+#define TSFCDE_E_STATE 9            /* stepping past level M, or a call in the wrong state        */
+#define TSFCDE_E_NO_DEVICE 10       /* no CUDA device / library built without a usable GPU        */
+
+/* ---- options -------------------------------------------------------------------------------- */
+#define TSFCDE_PRECOND_STRANG 0 /* Strang circulant s(.) of Eq. (3.7) (the paper's choice)       */
+#define TSFCDE_PRECOND_TCHAN 1  /* T. Chan's optimal circulant in place of s(.)                  */
+#define TSFCDE_PRECOND_NONE 2   /* plain CGS                                                     */
+
+#define TSFCDE_FP64 0 /* every step in float64 */
+
+typedef struct tsfcde_options {
+  int32_t precision;      /* TSFCDE_FP64                                                   */
+  int32_t preconditioner; /* TSFCDE_PRECOND_*; default STRANG                               */
+  double tol;             /* CGS stop: ||r_k||_2 / ||r_0||_2 < tol (Section 4); default 1e-12 */
+  int32_t maxit;          /* CGS iterations per level before E_NOT_CONVERGED; default 2000  */
+  int32_t device;         /* CUDA device ordinal; default 0                                 */
+  /* Separable source f(x,t) = sum_r T_r(t) X_r(x) (used when source_rank > 0, in which case the
+   * f callback of tsfcde_setup must be NULL):
+   *   source_x: source_rank rows of N values, X_r(x_i), row-major, host;
+   *   source_t: source_rank rows of M values, T_r(t_{j+sigma}) for j = 0..M-1, row-major, host.
+   * Both are copied during setup. */
+  int32_t source_rank;
+  const double *source_x;
+  const double *source_t;
+  int32_t levels_per_launch; /* device launches cover at most this many levels; 0 = no limit */
+  int32_t reserved[7];
+} tsfcde_options;
+
+/* Fill `opt` with the defaults above (the paper's settings: Strang, tol 1e-12, x0 = 0). */
+void tsfcde_default_options(tsfcde_options *opt);
+
+/* ---- statistics ----------------------------------------------------------------------------- */
+typedef struct tsfcde_stats {
+  int64_t level;            /* current level j: the context holds u^j                       */
+  int64_t levels_advanced;  /* levels advanced by the call that filled this struct          */
+  int64_t total_iterations; /* CGS iterations summed over those levels                      */
+  int32_t max_iterations;   /* largest per-level CGS iteration count among them             */
+  int32_t min_iterations;   /* smallest                                                     */
+  double max_residual;      /* largest final ||r||/||r_0|| among them                       */
+  int32_t status;           /* worst device status seen (a TSFCDE_* code)                   */
+  int32_t device_launches;  /* kernel launches the call made                                */
+} tsfcde_stats;
+
+/* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */
+/* gamma(t), d_plus(t), d_minus(t) of Eq. (1.1); called at t_{j+sigma} = (j+sigma) tau. */
+typedef double (*tsfcde_coef_fn)(double t, void *user);
+/* Vectorized field: out[i] = F(x[i], t) for i < n.  phi is called once with t = 0; f is called
+ * once per level with t = t_{j+sigma} (Eq. (2.1) evaluates f at t_{j+sigma}). */
+typedef void (*tsfcde_field_fn)(double t, const double *x, double *out, int64_t n, void *user);
+
+typedef struct tsfcde_ctx tsfcde_ctx;
+
+/* ---- life cycle ----------------------------------------------------------------------------- */
+
+/* Build a solver for one TSFCDE instance (Eq. (1.1) on the mesh of Section 2.1).
+ *   out       receives the context (set to NULL on failure).
+ *   a < b, T > 0, N >= 1 interior points, M >= 1 levels, 0 < alpha <= 1, 1 < beta <= 2.
+ *   gamma, d_plus, d_minus: required; d_plus, d_minus must be >= 0 at every t_{j+sigma}.
+ *   phi: required (initial value u^0_i = phi(x_i), Eq. (2.1)).
+ *   f: source, or NULL for f = 0 or for a separable source given through `opt`.
+ *   user: passed through to every callback.  opt: NULL for the defaults.
+ * Allocates on the device: O(N) vectors and spectra, the O(M N) history of increments
+ * u^{s+1} - u^s (FP64) that the L2-1_sigma sum of Lemma 1 reads at every level, and, when f is a
+ * callback, the M x N source table.  Computes on the device: the WSGD weights (Lemma 2), the
+ * L2-1_sigma coefficients (Lemma 1), the Toeplitz spectra of the circulant embedding, and the
+ * eigenvalues of the circulant approximations s(Q), s(W_beta).  Leaves the context at level 0. */
+int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int64_t M,
+                 double alpha, double beta, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus,
+                 tsfcde_coef_fn d_minus, tsfcde_field_fn phi, tsfcde_field_fn f, void *user,
+                 const tsfcde_options *opt);
+
+/* Advance `nsteps` levels (Algorithm "Practical implementation of IDS", one loop trip per
+ * level): history sum of Lemma 1, B u^j by FFT, + f, then preconditioned CGS for A u^{j+1} = g
+ * from a zero initial guess (Section 4).  Fails with E_STATE if the march would pass level M.
+ * `stats` may be NULL.  Runs asynchronously to nothing: returns when the levels are done. */
+int tsfcde_step(tsfcde_ctx *ctx, int64_t nsteps, tsfcde_stats *stats);
+
+/* Advance to level M and copy u^M (N values) to the host buffer u_out (may be NULL). */
+int tsfcde_solve(tsfcde_ctx *ctx, double *u_out, tsfcde_stats *stats);
+
+/* Copy the current level u^j to the host buffer u_out (N values); *level receives j. */
+int tsfcde_get_level(tsfcde_ctx *ctx, double *u_out, int64_t *level);
+
+/* Return to level 0.  u0: N host values to use as u^0, or NULL to keep phi(x_i). */
+int tsfcde_reset(tsfcde_ctx *ctx, const double *u0);
+
+/* Per-level CGS iteration counts and final relative residuals of the levels advanced so far:
+ * iters[j] and resid[j] for j < count <= current level (either pointer may be NULL). */
+int tsfcde_get_history(tsfcde_ctx *ctx, int32_t *iters, double *resid, int64_t count);
+
+/* Diagnostic products with the level-j operators (Eq. (3.3), Eq. (3.7)), computed by the same
+ * device kernels as the march: op = 0: y = A^{(j+sigma)} x, 1: y = B^{(j+sigma)} x,
+ * 2: y = (P^{(j+sigma)})^{-1} x.  x, y: N host values.  Does not change the march state. */
+#define TSFCDE_OP_A 0
+#define TSFCDE_OP_B 1
+#define TSFCDE_OP_PINV 2
+int tsfcde_apply(tsfcde_ctx *ctx, int32_t op, int64_t j, const double *x, double *y);
+
+/* Release everything the context holds.  NULL is allowed. */
+void tsfcde_free(tsfcde_ctx *ctx);
+
+/* Static text for a status code. */
+const char *tsfcde_strerror(int status);
+
+/* Library version string. */
+const char *tsfcde_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSFCDE_H */

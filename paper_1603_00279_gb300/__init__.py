@@ -1,0 +1,237 @@
+"""Python binding of libtsfcde (include/tsfcde.h): argument marshalling only.
+
+Every step of the time march runs in the CUDA library; this module converts Python callables and
+numpy arrays to the plain pointers of the C ABI and raises on error status.  If the compiled
+library is missing, importing the functions raises: there is no CPU fallback.
+
+    from paper_1603_00279_gb300 import Solver
+    s = Solver(a, b, T, N, M, alpha, beta, gamma, d_plus, d_minus, phi, f, preconditioner="strang")
+    u = s.solve()          # u^M at the N interior nodes
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Callable, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtsfcde.so")
+
+TSFCDE_OK = 0
+STATUS_NAMES = {
+    0: "OK", 1: "E_INVALID_ARG", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONFINITE",
+    5: "E_NOT_CONVERGED", 6: "E_BREAKDOWN", 7: "E_SINGULAR_PRECOND", 8: "E_TIMEOUT",
+    9: "E_STATE", 10: "E_NO_DEVICE",
+}
+PRECONDITIONERS = {"strang": 0, "tchan": 1, "none": 2}
+OPS = {"A": 0, "B": 1, "Pinv": 2}
+
+COEF_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
+FIELD_FN = C.CFUNCTYPE(None, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                       C.c_int64, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("preconditioner", C.c_int32), ("tol", C.c_double),
+                ("maxit", C.c_int32), ("device", C.c_int32), ("source_rank", C.c_int32),
+                ("source_x", C.POINTER(C.c_double)), ("source_t", C.POINTER(C.c_double)),
+                ("levels_per_launch", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("level", C.c_int64), ("levels_advanced", C.c_int64),
+                ("total_iterations", C.c_int64), ("max_iterations", C.c_int32),
+                ("min_iterations", C.c_int32), ("max_residual", C.c_double),
+                ("status", C.c_int32), ("device_launches", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TsfcdeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> C.CDLL:
+    """Load libtsfcde.so (built by paper_1603_00279_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libtsfcde.so not built ({p}); run paper_1603_00279_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    pd = C.POINTER(C.c_double)
+    lib.tsfcde_default_options.argtypes = [C.POINTER(Options)]
+    lib.tsfcde_default_options.restype = None
+    lib.tsfcde_setup.argtypes = [C.POINTER(vp), dbl, dbl, dbl, i64, i64, dbl, dbl, COEF_FN, COEF_FN,
+                                 COEF_FN, FIELD_FN, FIELD_FN, vp, C.POINTER(Options)]
+    lib.tsfcde_setup.restype = C.c_int
+    lib.tsfcde_step.argtypes = [vp, i64, C.POINTER(Stats)]
+    lib.tsfcde_step.restype = C.c_int
+    lib.tsfcde_solve.argtypes = [vp, pd, C.POINTER(Stats)]
+    lib.tsfcde_solve.restype = C.c_int
+    lib.tsfcde_get_level.argtypes = [vp, pd, C.POINTER(i64)]
+    lib.tsfcde_get_level.restype = C.c_int
+    lib.tsfcde_reset.argtypes = [vp, pd]
+    lib.tsfcde_reset.restype = C.c_int
+    lib.tsfcde_get_history.argtypes = [vp, C.POINTER(i32), pd, i64]
+    lib.tsfcde_get_history.restype = C.c_int
+    lib.tsfcde_apply.argtypes = [vp, i32, i64, pd, pd]
+    lib.tsfcde_apply.restype = C.c_int
+    lib.tsfcde_free.argtypes = [vp]
+    lib.tsfcde_free.restype = None
+    lib.tsfcde_strerror.argtypes = [C.c_int]
+    lib.tsfcde_strerror.restype = C.c_char_p
+    lib.tsfcde_version.argtypes = []
+    lib.tsfcde_version.restype = C.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(st: int, where: str, allow_not_converged: bool = False):
+    if st == TSFCDE_OK or (allow_not_converged and st == 5):
+        return
+    raise TsfcdeError(st, where)
+
+
+class Solver:
+    """One TSFCDE instance on the GPU (wraps tsfcde_setup ... tsfcde_free).
+
+    gamma, d_plus, d_minus: callables t -> float.  phi: callable x (ndarray) -> ndarray.
+    f: callable (x ndarray, t) -> ndarray, or None; alternatively `separable` = list of
+    (T_r(t), X_r(x)) pairs, evaluated here on the grid and passed as the separable source.
+    """
+
+    def __init__(self, a, b, T, N, M, alpha, beta, gamma: Callable, d_plus: Callable,
+                 d_minus: Callable, phi: Callable, f: Optional[Callable] = None,
+                 separable=None, preconditioner: str = "strang", tol: float = 1e-12,
+                 maxit: int = 2000, device: int = 0, levels_per_launch: int = 0):
+        self.lib = load_library()
+        self.N, self.M = int(N), int(M)
+        self.h = (b - a) / (N + 1)
+        self.tau = T / M
+        sigma = 1.0 - alpha / 2.0
+        self._keep = []
+
+        def coef(fn):
+            cb = COEF_FN(lambda t, _u: float(fn(t)))
+            self._keep.append(cb)
+            return cb
+
+        def field(fn, with_t):
+            def call(t, xp, outp, n, _u):
+                x = np.ctypeslib.as_array(xp, shape=(n,))
+                out = np.ctypeslib.as_array(outp, shape=(n,))
+                out[:] = fn(x, t) if with_t else fn(x)
+            cb = FIELD_FN(call)
+            self._keep.append(cb)
+            return cb
+
+        opt = Options()
+        self.lib.tsfcde_default_options(C.byref(opt))
+        opt.preconditioner = PRECONDITIONERS[preconditioner]
+        opt.tol = tol
+        opt.maxit = maxit
+        opt.device = device
+        opt.levels_per_launch = levels_per_launch
+        f_cb = FIELD_FN() if f is None else field(f, True)
+        if separable is not None:
+            if f is not None:
+                raise ValueError("give either f or separable")
+            x = a + self.h * np.arange(1, N + 1, dtype=np.float64)
+            ts = (np.arange(M, dtype=np.float64) + sigma) * self.tau
+            sx = np.ascontiguousarray([np.broadcast_to(Xr(x), x.shape) for _, Xr in separable],
+                                      dtype=np.float64)
+            st = np.ascontiguousarray([[Tr(t) for t in ts] for Tr, _ in separable], dtype=np.float64)
+            self._keep += [sx, st]
+            opt.source_rank = len(separable)
+            opt.source_x = _dptr(sx)
+            opt.source_t = _dptr(st)
+        ctx = C.c_void_p()
+        stt = self.lib.tsfcde_setup(C.byref(ctx), a, b, T, self.N, self.M, alpha, beta, coef(gamma),
+                                    coef(d_plus), coef(d_minus), field(phi, False), f_cb, None,
+                                    C.byref(opt))
+        _check(stt, "tsfcde_setup")
+        self.ctx = ctx
+
+    @classmethod
+    def from_problem(cls, prob, source: str = "callback", **kw):
+        """Build from a tsfcde_workloads.Problem-like object."""
+        f = prob.f if source == "callback" else None
+        sep = prob.separable if source == "separable" else None
+        if source == "separable" and sep is None:
+            f = None
+        return cls(prob.a, prob.b, prob.T, prob.n, prob.M, prob.alpha, prob.beta, prob.gamma,
+                   prob.d_plus, prob.d_minus, prob.phi, f, separable=sep,
+                   preconditioner=kw.pop("preconditioner", prob.preconditioner),
+                   tol=kw.pop("tol", prob.tol), **kw)
+
+    def step(self, nsteps: int = 1) -> dict:
+        s = Stats()
+        _check(self.lib.tsfcde_step(self.ctx, nsteps, C.byref(s)), "tsfcde_step", True)
+        return s.as_dict()
+
+    def solve(self, out: Optional[np.ndarray] = None):
+        out = np.empty(self.N) if out is None else out
+        s = Stats()
+        _check(self.lib.tsfcde_solve(self.ctx, _dptr(out), C.byref(s)), "tsfcde_solve", True)
+        self.last_stats = s.as_dict()
+        return out
+
+    def get_level(self):
+        out = np.empty(self.N)
+        j = C.c_int64()
+        _check(self.lib.tsfcde_get_level(self.ctx, _dptr(out), C.byref(j)), "tsfcde_get_level")
+        return out, j.value
+
+    def reset(self, u0: Optional[np.ndarray] = None):
+        p = None if u0 is None else _dptr(np.ascontiguousarray(u0, dtype=np.float64))
+        _check(self.lib.tsfcde_reset(self.ctx, p), "tsfcde_reset")
+
+    def history(self, count: int):
+        it = np.zeros(count, dtype=np.int32)
+        rs = np.zeros(count)
+        _check(self.lib.tsfcde_get_history(self.ctx, it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           _dptr(rs), count), "tsfcde_get_history")
+        return it, rs
+
+    def apply(self, op: str, j: int, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.N)
+        _check(self.lib.tsfcde_apply(self.ctx, OPS[op], j, _dptr(x), _dptr(y)), "tsfcde_apply")
+        return y
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.tsfcde_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def strerror(status: int) -> str:
+    return load_library().tsfcde_strerror(status).decode()

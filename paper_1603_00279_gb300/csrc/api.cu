@@ -1,0 +1,473 @@
+// Host side of the C ABI declared in include/tsfcde.h: argument checks, the per-level coefficient
+// tables (the user's gamma, d_+, d_- are host callbacks, evaluated once per level at
+// t_{j+sigma}), device memory, and the cooperative launches of level_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/tsfcde.h"
+#include "tsfcde_internal.cuh"
+
+using tsf::Args;
+
+struct tsfcde_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, M = 0;
+  double a = 0, b = 0, T = 0, alpha = 0, beta = 0, h = 0, tau = 0, sigma = 0;
+  tsfcde_options opt;
+  Args A;
+  int grid = 0;
+  size_t smem = 0;
+  int64_t level = 0;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  double *ring = nullptr;
+  std::vector<double> u0;
+  double *omega = nullptr, *gtmp = nullptr;
+  double2 *BhF = nullptr;
+  double *gam = nullptr, *dp = nullptr, *dm = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TSFCDE_OK;
+  if (e == cudaErrorMemoryAllocation) return TSFCDE_E_NOMEM;
+  return TSFCDE_E_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+// Bump allocator over one device arena, 256-byte aligned pieces.
+struct Carver {
+  size_t off = 0;
+  char *base = nullptr;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+bool all_finite(const double *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+int device_status(tsfcde_ctx *c, int *st) {
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, c->A.status, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *st = h[0];
+  return TSFCDE_OK;
+}
+
+int reset_device_flags(tsfcde_ctx *c) {
+  CK(cudaMemsetAsync(c->A.bar, 0, 64 * sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->A.status, 0, 4 * sizeof(int), c->stream));
+  return TSFCDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsfcde_default_options(tsfcde_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = TSFCDE_FP64;
+  opt->preconditioner = TSFCDE_PRECOND_STRANG;
+  opt->tol = 1e-12;
+  opt->maxit = 2000;
+  opt->device = 0;
+  opt->source_rank = 0;
+  opt->levels_per_launch = 0;
+}
+
+const char *tsfcde_strerror(int status) {
+  switch (status) {
+    case TSFCDE_OK: return "ok";
+    case TSFCDE_E_INVALID_ARG: return "invalid argument";
+    case TSFCDE_E_NOMEM: return "out of memory";
+    case TSFCDE_E_CUDA: return "CUDA runtime error";
+    case TSFCDE_E_NONFINITE: return "non-finite value";
+    case TSFCDE_E_NOT_CONVERGED: return "CGS did not converge within maxit on some level";
+    case TSFCDE_E_BREAKDOWN: return "CGS breakdown";
+    case TSFCDE_E_SINGULAR_PRECOND: return "singular circulant preconditioner";
+    case TSFCDE_E_TIMEOUT: return "device barrier wait timed out";
+    case TSFCDE_E_STATE: return "invalid state for this call";
+    case TSFCDE_E_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+const char *tsfcde_version(void) { return "tsfcde-gb300 0.1 (sm_103a)"; }
+
+void tsfcde_free(tsfcde_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->ring) cudaFree(c->ring);
+  if (c->arena) cudaFree(c->arena);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus,
+                      tsfcde_coef_fn d_minus, tsfcde_field_fn phi, tsfcde_field_fn f, void *user) {
+  const int64_t n = c->n, M = c->M;
+  // ---- host tables: callbacks at t_{j+sigma} (Eq. (2.1)) ----
+  std::vector<double> xg(n), gam(M), dp(M), dm(M);
+  for (int64_t i = 0; i < n; ++i) xg[i] = c->a + (double)(i + 1) * c->h;
+  c->u0.assign(n, 0.0);
+  phi(0.0, xg.data(), c->u0.data(), n, user);
+  if (!all_finite(c->u0.data(), n)) return TSFCDE_E_NONFINITE;
+  std::vector<int> newsym(M, 0);
+  for (int64_t j = 0; j < M; ++j) {
+    const double t = ((double)j + c->sigma) * c->tau;
+    gam[j] = gamma(t, user);
+    dp[j] = d_plus(t, user);
+    dm[j] = d_minus(t, user);
+    if (!std::isfinite(gam[j]) || !std::isfinite(dp[j]) || !std::isfinite(dm[j])) return TSFCDE_E_NONFINITE;
+    if (dp[j] < 0.0 || dm[j] < 0.0) return TSFCDE_E_INVALID_ARG;
+    newsym[j] = (j <= 1) || gam[j] != gam[j - 1] || dp[j] != dp[j - 1] || dm[j] != dm[j - 1];
+  }
+  const int R = c->opt.source_rank;
+  std::vector<double> fdense;
+  if (f) {
+    fdense.resize((size_t)M * n);
+    for (int64_t j = 0; j < M; ++j) {
+      const double t = ((double)j + c->sigma) * c->tau;
+      f(t, xg.data(), fdense.data() + (size_t)j * n, n, user);
+    }
+    if (!all_finite(fdense.data(), fdense.size())) return TSFCDE_E_NONFINITE;
+  }
+  if (R > 0) {
+    if (!all_finite(c->opt.source_x, (size_t)R * n) || !all_finite(c->opt.source_t, (size_t)R * M))
+      return TSFCDE_E_NONFINITE;
+  }
+
+  // ---- plans ----
+  Args &A = c->A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = (int)n;
+  A.M = (int)M;
+  const int lgL = std::max(3, ilog2(2 * n));
+  A.cp.lgL = lgL;
+  A.cp.L = 1 << lgL;
+  A.cp.lgN = lgL - 1;
+  A.cp.N = 1 << A.cp.lgN;
+  A.cp.lg1 = A.cp.lgN / 2;
+  A.cp.lg2 = A.cp.lgN - A.cp.lg1;
+  A.cp.N1 = 1 << A.cp.lg1;
+  A.cp.N2 = 1 << A.cp.lg2;
+  A.bp.lgNc = lgL;
+  A.bp.Nc = 1 << lgL;
+  A.bp.lg1 = lgL / 2;
+  A.bp.lg2 = lgL - A.bp.lg1;
+  A.bp.N1 = 1 << A.bp.lg1;
+  A.bp.N2 = 1 << A.bp.lg2;
+  const int L = A.cp.L, N = A.cp.N;
+  A.precond = c->opt.preconditioner;
+  A.sigma = c->sigma;
+  A.hscale = std::pow(c->tau, -c->alpha) / std::tgamma(2.0 - c->alpha);
+  A.tol = c->opt.tol;
+  A.maxit = c->opt.maxit;
+  A.src_rank = R;
+
+  // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, c->device));
+  c->grid = prop.multiProcessorCount;
+  const int G = c->grid;
+  const int budget = 4096;   // complex values per ping-pong buffer
+  auto cap = [&](int items, int lines_per_item, int lg) {
+    const int per = (items + G - 1) / G;
+    const int fit = std::max(1, (budget >> lg) / lines_per_item);
+    return std::max(1, std::min(per, fit));
+  };
+  A.cap_col = cap(A.cp.N2, 1, A.cp.lg1);
+  A.cap_row = cap(A.cp.N1 / 2 + 1, 2, A.cp.lg2);
+  A.cap_bcol = cap(A.bp.N2, 1, A.bp.lg1);
+  A.cap_brow = cap(A.bp.N1, 1, A.bp.lg2);
+  c->smem = tsf::level_smem_bytes(A);
+  if (c->smem > prop.sharedMemPerBlockOptin) return TSFCDE_E_INVALID_ARG;
+  for (const void *fn : {tsf::level_kernel_ptr(), tsf::apply_kernel_ptr(), tsf::setup_kernel_ptr()}) {
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
+    if (occ < 1) return TSFCDE_E_INVALID_ARG;
+  }
+
+  // ---- device memory: one arena + the history ring ----
+  const size_t Lp = (size_t)L;
+  Carver cv;
+  for (int pass = 0; pass < 2; ++pass) {
+    cv.off = 0;
+    cv.base = pass ? c->arena : nullptr;
+    A.u = cv.take<double>(Lp);
+    A.x = cv.take<double>(Lp);
+    A.r = cv.take<double>(Lp);
+    A.rt = cv.take<double>(Lp);
+    A.p = cv.take<double>(Lp);
+    A.q = cv.take<double>(Lp);
+    A.uu = cv.take<double>(Lp);
+    A.vh = cv.take<double>(Lp);
+    A.H = cv.take<double>(Lp);
+    A.Y1 = cv.take<double2>(Lp);
+    A.Y2 = cv.take<double2>(Lp);
+    A.SA = cv.take<double2>(N + 1);
+    A.SB = cv.take<double2>(N + 1);
+    A.SP = cv.take<double2>(N + 1);
+    double2 *What = cv.take<double2>(N + 1);
+    double2 *LamW = cv.take<double2>(n);
+    double2 *LamQ = cv.take<double2>(n);
+    double2 *chirp = cv.take<double2>(n);
+    double2 *BhI = cv.take<double2>(Lp);
+    c->BhF = cv.take<double2>(Lp);
+    double2 *tw = cv.take<double2>(Lp);
+    A.What = What;
+    A.LamW = LamW;
+    A.LamQ = LamQ;
+    A.chirpI = chirp;
+    A.BhI = BhI;
+    A.twL = tw;
+    A.cprime = cv.take<double>(n);
+    double *eta = cv.take<double>(M), *q = cv.take<double>(M), *kp = cv.take<double>(M),
+           *km = cv.take<double>(M);
+    A.lv_eta = eta;
+    A.lv_q = q;
+    A.lv_kp = kp;
+    A.lv_km = km;
+    A.lv_newsym = cv.take<int>(M);
+    A.hc = cv.take<double>(M + 2);
+    A.hl = cv.take<double>(M + 2);
+    c->gam = cv.take<double>(M);
+    c->dp = cv.take<double>(M);
+    c->dm = cv.take<double>(M);
+    A.partials = cv.take<double>((size_t)2 * G * 4);
+    A.bar = cv.take<unsigned>(64);
+    A.status = cv.take<int>(4);
+    A.iters = cv.take<int>(M);
+    A.resid = cv.take<double>(M);
+    c->omega = cv.take<double>(n + 2);
+    c->gtmp = cv.take<double>(n + 2);
+    A.f_dense = f ? cv.take<double>((size_t)M * n) : nullptr;
+    A.src_x = R > 0 ? cv.take<double>((size_t)R * n) : nullptr;
+    A.src_t = R > 0 ? cv.take<double>((size_t)R * M) : nullptr;
+    if (!pass) {
+      c->arena_bytes = cv.off + 256;
+      CK(cudaMalloc(&c->arena, c->arena_bytes));
+      CK(cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream));
+    }
+  }
+  A.ring_stride = (long long)((n + 31) / 32 * 32);
+  const size_t ring_bytes = (size_t)M * (size_t)A.ring_stride * sizeof(double);
+  CK(cudaMalloc(&c->ring, ring_bytes));
+  CK(cudaMemsetAsync(c->ring, 0, ring_bytes, c->stream));
+  A.ring = c->ring;
+
+  // ---- uploads ----
+  CK(cudaMemcpyAsync(c->gam, gam.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dp, dp.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dm, dm.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync((void *)A.lv_newsym, newsym.data(), M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (f)
+    CK(cudaMemcpyAsync((void *)A.f_dense, fdense.data(), fdense.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, c->stream));
+  if (R > 0) {
+    CK(cudaMemcpyAsync((void *)A.src_x, c->opt.source_x, (size_t)R * n * sizeof(double),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((void *)A.src_t, c->opt.source_t, (size_t)R * M * sizeof(double),
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaMemcpyAsync(A.u, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+
+  // ---- device setup: weights (Lemma 2), time tables (Lemma 1), spectra ----
+  int st = tsf::launch_weights(c->omega, c->gtmp, (int)n, c->beta, c->stream);
+  if (st) return st;
+  st = tsf::launch_time_tables((int)M, c->alpha, c->tau, c->h, c->beta, c->gam, c->dp, c->dm,
+                               (double *)A.hc, (double *)A.hl, (double *)A.lv_eta, (double *)A.lv_q,
+                               (double *)A.lv_kp, (double *)A.lv_km, c->stream);
+  if (st) return st;
+  st = reset_device_flags(c);
+  if (st) return st;
+  st = tsf::launch_setup(A, c->grid, c->smem, c->stream, c->omega, (double2 *)A.What, (double2 *)A.LamW,
+                         (double2 *)A.LamQ, (double2 *)A.BhI, c->BhF, (double2 *)A.chirpI,
+                         (double2 *)A.twL, c->beta, A.precond);
+  if (st) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  int dst = 0;
+  st = device_status(c, &dst);
+  if (st) return st;
+  if (dst) return dst;
+  c->level = 0;
+  return TSFCDE_OK;
+}
+
+int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int64_t M,
+                 double alpha, double beta, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus,
+                 tsfcde_coef_fn d_minus, tsfcde_field_fn phi, tsfcde_field_fn f, void *user,
+                 const tsfcde_options *opt) {
+  if (!out) return TSFCDE_E_INVALID_ARG;
+  *out = nullptr;
+  if (!(a < b) || !(T > 0) || N < 1 || M < 1 || !(alpha > 0.0 && alpha <= 1.0) ||
+      !(beta > 1.0 && beta <= 2.0) || !gamma || !d_plus || !d_minus || !phi)
+    return TSFCDE_E_INVALID_ARG;
+  if (N > (int64_t(1) << 22) - 1 || M > (int64_t(1) << 30)) return TSFCDE_E_INVALID_ARG;
+  tsfcde_options o;
+  tsfcde_default_options(&o);
+  if (opt) o = *opt;
+  if (o.preconditioner < 0 || o.preconditioner > 2 || o.precision != TSFCDE_FP64 || !(o.tol > 0) ||
+      o.maxit < 1 || o.source_rank < 0 || (o.source_rank > 0 && (!o.source_x || !o.source_t || f)))
+    return TSFCDE_E_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
+  tsfcde_ctx *c = new tsfcde_ctx();
+  c->device = o.device;
+  c->opt = o;
+  c->n = N;
+  c->M = M;
+  c->a = a;
+  c->b = b;
+  c->T = T;
+  c->alpha = alpha;
+  c->beta = beta;
+  c->h = (b - a) / (double)(N + 1);
+  c->tau = T / (double)M;
+  c->sigma = 1.0 - alpha / 2.0;
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return TSFCDE_E_CUDA;
+  }
+  const int st = setup_impl(c, gamma, d_plus, d_minus, phi, f, user);
+  if (st != TSFCDE_OK) {
+    tsfcde_free(c);
+    return st;
+  }
+  *out = c;
+  return TSFCDE_OK;
+}
+
+int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
+  if (!c || nsteps < 0) return TSFCDE_E_INVALID_ARG;
+  if (c->level + nsteps > c->M) return TSFCDE_E_STATE;
+  CK(cudaSetDevice(c->device));
+  const int64_t j0 = c->level, j1 = c->level + nsteps;
+  const int64_t chunk = c->opt.levels_per_launch > 0 ? c->opt.levels_per_launch : nsteps;
+  int launches = 0, worst = TSFCDE_OK;
+  for (int64_t s = j0; s < j1; s += chunk) {
+    const int64_t e = std::min(j1, s + chunk);
+    int st = reset_device_flags(c);
+    if (st) return st;
+    st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
+    if (st) return st;
+    ++launches;
+    CK(cudaStreamSynchronize(c->stream));
+    int dst = 0;
+    st = device_status(c, &dst);
+    if (st) return st;
+    if (dst != TSFCDE_OK && dst != TSFCDE_E_NOT_CONVERGED) return dst;
+    if (dst == TSFCDE_E_NOT_CONVERGED) worst = dst;
+    c->level = e;
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->level = c->level;
+    stats->levels_advanced = nsteps;
+    stats->status = worst;
+    stats->device_launches = launches;
+    if (nsteps > 0) {
+      std::vector<int> it(nsteps);
+      std::vector<double> rs(nsteps);
+      CK(cudaMemcpy(it.data(), c->A.iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(rs.data(), c->A.resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+      stats->min_iterations = it[0];
+      for (int64_t k = 0; k < nsteps; ++k) {
+        stats->total_iterations += it[k];
+        stats->max_iterations = std::max(stats->max_iterations, it[k]);
+        stats->min_iterations = std::min(stats->min_iterations, it[k]);
+        stats->max_residual = std::max(stats->max_residual, rs[k]);
+      }
+    }
+  }
+  return worst;
+}
+
+int tsfcde_get_level(tsfcde_ctx *c, double *u_out, int64_t *level) {
+  if (!c) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  if (level) *level = c->level;
+  if (u_out) {
+    CK(cudaMemcpyAsync(u_out, c->A.u, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return TSFCDE_OK;
+}
+
+int tsfcde_solve(tsfcde_ctx *c, double *u_out, tsfcde_stats *stats) {
+  if (!c) return TSFCDE_E_INVALID_ARG;
+  const int st = tsfcde_step(c, c->M - c->level, stats);
+  if (st != TSFCDE_OK && st != TSFCDE_E_NOT_CONVERGED) return st;
+  const int st2 = tsfcde_get_level(c, u_out, nullptr);
+  return st2 ? st2 : st;
+}
+
+int tsfcde_reset(tsfcde_ctx *c, const double *u0) {
+  if (!c) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  const double *src = u0 ? u0 : c->u0.data();
+  if (u0 && !all_finite(u0, c->n)) return TSFCDE_E_NONFINITE;
+  CK(cudaMemcpyAsync(c->A.u, src, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->level = 0;
+  return TSFCDE_OK;
+}
+
+int tsfcde_get_history(tsfcde_ctx *c, int32_t *iters, double *resid, int64_t count) {
+  if (!c || count < 0 || count > c->level) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  if (count == 0) return TSFCDE_OK;
+  if (iters) CK(cudaMemcpy(iters, c->A.iters, count * sizeof(int), cudaMemcpyDeviceToHost));
+  if (resid) CK(cudaMemcpy(resid, c->A.resid, count * sizeof(double), cudaMemcpyDeviceToHost));
+  return TSFCDE_OK;
+}
+
+int tsfcde_apply(tsfcde_ctx *c, int32_t op, int64_t j, const double *x, double *y) {
+  if (!c || !x || !y || op < 0 || op > 2 || j < 0 || j >= c->M) return TSFCDE_E_INVALID_ARG;
+  if (op == TSFCDE_OP_PINV && c->A.precond == TSFCDE_PRECOND_NONE) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  // vh and H are rewritten by every level before use, so they serve as scratch here
+  CK(cudaMemcpyAsync(c->A.vh, x, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int st = reset_device_flags(c);
+  if (st) return st;
+  st = tsf::launch_apply(c->A, c->grid, c->smem, c->stream, op, (int)j, c->A.vh, c->A.H);
+  if (st) return st;
+  CK(cudaMemcpyAsync(y, c->A.H, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int dst = 0;
+  st = device_status(c, &dst);
+  if (st) return st;
+  return dst;
+}
+
+}  // extern "C"

@@ -1,0 +1,864 @@
+// Device side of the level solve (Algorithm "Practical implementation of IDS", arXiv:1603.00279
+// Section 3.2) as persistent cooperative kernels.  One launch advances a range of levels; every
+// phase below is separated from the next by a bounded grid barrier, so each level costs a fixed
+// sequence of phases and no host round trip:
+//
+//   symbols  (when the level operators change):  Lambda_P -> 1/Lambda_P -> inverse n-point DFT
+//            by Bluestein (3 phases) -> Toeplitz embedding of P^{-1}'s circulant column ->
+//            forward FFT and the spectra of A, B, P^{-1} (2 phases)               [Eq. (3.7)]
+//   RHS      commit of the previous level + history sum of Lemma 1 + column FFT of u^j; row
+//            pass with B's spectrum; column pass giving g = B u^j - hscale*H + f  [Eq. (3.1)]
+//   CGS      preconditioned CGS from x0 = 0 (Section 4), the elementwise updates and dot
+//            products fused into the column passes of the FFT convolutions; each iteration is
+//            10 phases (P^{-1} p, A p^, dot, q/w update, P^{-1} w, A u^, dots).
+#include "tsfcde_internal.cuh"
+
+namespace tsf {
+
+// ------------------------------------------------------------------------------------------------
+// per-CTA shared memory view
+// ------------------------------------------------------------------------------------------------
+struct Smem {
+  double2 *a, *b;   // ping-pong line buffers
+  double *red;      // reduction scratch (4 * 32 doubles)
+};
+
+__device__ __forceinline__ Smem smem_view(int lp_max) {
+  extern __shared__ double2 dsm[];
+  Smem s;
+  s.a = dsm;
+  s.b = dsm + lp_max;
+  s.red = reinterpret_cast<double *>(dsm + 2 * lp_max);
+  return s;
+}
+
+__device__ __forceinline__ int lp_max_of(const Args &A) {
+  int m = A.cap_col << A.cp.lg1;
+  m = max(m, (2 * A.cap_row) << A.cp.lg2);
+  m = max(m, A.cap_bcol << A.bp.lg1);
+  m = max(m, A.cap_brow << A.bp.lg2);
+  return m;
+}
+
+// Contiguous item range of this CTA: [lo, hi).
+__device__ __forceinline__ void my_items(int nitems, int &lo, int &hi) {
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  lo = min(nitems, blockIdx.x * per);
+  hi = min(nitems, lo + per);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Column pass of a four-step FFT: lines of P1 = 2^lg1 points, 2^lg2 of them, element m = m1*P2+m2.
+// INV: line m2 loads Yin[k1*P2 + m2] * conj(W^{m2 k1}) and is inverse-transformed.
+// body(m, z) -> next forward input (z: inverse result when INV, otherwise undefined).
+// FWD: forward transform of body's outputs, twiddle W^{m2 k1}, store Yout[k1*P2 + m2].
+// W^{e} = twL[e << tws] (tws = 1 for the half-length conv plan, 0 for the length-L plan).
+// ------------------------------------------------------------------------------------------------
+template <bool INV, bool FWD, class Body>
+__device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, int lg2, int tws,
+                                         int cap, const double2 *__restrict__ Yin,
+                                         double2 *__restrict__ Yout, Body body) {
+  const int P1 = 1 << lg1, P2 = 1 << lg2;
+  const double2 *__restrict__ tw = A.twL;
+  const int lgT = A.cp.lgL;
+  int lo, hi;
+  my_items(P2, lo, hi);
+  for (int c0 = lo; c0 < hi; c0 += cap) {
+    const int cnt = min(cap, hi - c0);
+    double2 *a = S.a, *b = S.b;
+    if (INV) {
+      for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
+        const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
+        a[(l << lg1) + k1] = cmulc(Yin[(k1 << lg2) + m2], __ldg(tw + ((m2 * k1) << tws)));
+      }
+      __syncthreads();
+      a = smem_fft<+1>(a, b, lg1, cnt, tw, lgT);
+      b = (a == S.a) ? S.b : S.a;
+    }
+    for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
+      const int l = e % cnt, m1 = e / cnt, m2 = c0 + l;
+      const int idx = (l << lg1) + m1;
+      a[idx] = body((m1 << lg2) + m2, a[idx]);
+    }
+    __syncthreads();
+    if (FWD) {
+      a = smem_fft<-1>(a, b, lg1, cnt, tw, lgT);
+      for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
+        const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
+        Yout[(k1 << lg2) + m2] = cmul(a[(l << lg1) + k1], __ldg(tw + ((m2 * k1) << tws)));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Row pass of the half-length (real-input) convolution plan.  Item it < N1/2+1 holds rows
+// (ka, kb) = (it, N1-it) (rows 0 and N1/2 pair with themselves).  After the forward row FFTs,
+// Z_k and Z_{N-k} sit in the same item, which is what the real-FFT split needs:
+//   X_k = (E2 + w O2)/2, X_{k+N} = (E2 - w O2)/2, E2 = Z_k + conj Z_{N-k},
+//   O2 = -i (Z_k - conj Z_{N-k}), w = e^{-2 pi i k / L}.
+// MODE 0 (convolve): Y = S X at k and k+N (S_{k+N} = conj S_{N-k}, S_N stored at slot N), then
+//   the inverse split and the inverse row FFTs; result to Y2.  Spectra are pre-scaled by 1/(4N).
+// MODE 1 (spectrum): store X_k (times `scale`) into Sout at slot(k) and X_N at slot N, and, when
+//   sym != 0, also the spectra of A and B of level j at the same slots.
+// ------------------------------------------------------------------------------------------------
+struct LevelScalars {
+  double eta, q, kp, km;
+};
+
+__device__ __forceinline__ LevelScalars level_scalars(const Args &A, int j) {
+  LevelScalars s;
+  s.eta = A.lv_eta[j];
+  s.q = A.lv_q[j];
+  s.kp = A.lv_kp[j];
+  s.km = A.lv_km[j];
+  return s;
+}
+
+// Spectra of A = eta I - sigma L and B = eta I + (1-sigma) L at frequency k of the L-embedding,
+// L = q Q + kp W + km W^T; Q's symbol is 2 i sin(2 pi k / L), W^T's is conj(W's).  Scaled 1/(4N).
+__device__ __forceinline__ void ab_symbols(const Args &A, const LevelScalars &s, double2 w_k,
+                                           bool nyq, double2 Wk, double2 &sa, double2 &sb) {
+  const double qs = nyq ? 0.0 : -2.0 * w_k.y;   // Im of Q's symbol (real part 0)
+  const double lre = (s.kp + s.km) * Wk.x;
+  const double lim = s.q * qs + (s.kp - s.km) * Wk.y;
+  const double sc = 1.0 / (4.0 * (double)A.cp.N);
+  sa = make_double2((s.eta - A.sigma * lre) * sc, (-A.sigma * lim) * sc);
+  sb = make_double2((s.eta + (1.0 - A.sigma) * lre) * sc, ((1.0 - A.sigma) * lim) * sc);
+}
+
+template <int MODE>
+__device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const double2 *__restrict__ Sym,
+                                         double2 *__restrict__ Sout, double scale, int sym_level) {
+  const ConvPlan &P = A.cp;
+  const int N1 = P.N1, N2 = P.N2, lg2 = P.lg2, N = P.N;
+  const double2 *__restrict__ tw = A.twL;
+  const int nitems = N1 / 2 + 1;
+  int lo, hi;
+  my_items(nitems, lo, hi);
+  LevelScalars ls;
+  if (MODE == 1 && sym_level >= 0) ls = level_scalars(A, sym_level);
+  for (int i0 = lo; i0 < hi; i0 += A.cap_row) {
+    const int cnt = min(A.cap_row, hi - i0);
+    const int nl = 2 * cnt;
+    double2 *a = S.a, *b = S.b;
+    // load: line 2t = row ka, line 2t+1 = row kb
+    for (int e = threadIdx.x; e < nl * N2; e += blockDim.x) {
+      const int line = e >> lg2, k2 = e & (N2 - 1);
+      const int it = i0 + (line >> 1);
+      const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
+      a[e] = A.Y1[(row << lg2) + k2];
+    }
+    __syncthreads();
+    a = smem_fft<-1>(a, b, lg2, nl, tw, P.lgL);
+    b = (a == S.a) ? S.b : S.a;
+    // split / multiply / merge, pairwise in k and N-k
+    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
+      const int t = e >> lg2, k2 = e & (N2 - 1);
+      const int it = i0 + t;
+      const int ka = it, kb = (N1 - it) & (N1 - 1);
+      double2 *ra = a + ((2 * t) << lg2);
+      double2 *rb = (ka == kb) ? ra : a + ((2 * t + 1) << lg2);
+      int k2p;
+      if (ka == 0) {
+        if (k2 > N2 / 2) continue;
+        k2p = (N2 - k2) & (N2 - 1);
+      } else if (ka == kb) {   // row N1/2
+        if (k2 >= N2 / 2) continue;
+        k2p = N2 - 1 - k2;
+      } else {
+        k2p = N2 - 1 - k2;
+      }
+      const int k = ka + N1 * k2;
+      const double2 Zk = ra[k2], Zp = rb[k2p];
+      const double2 w = __ldg(tw + k);
+      const double2 Zc = cconj(Zp);
+      const double2 E2 = cadd(Zk, Zc);
+      const double2 O2 = mul_mi(csub(Zk, Zc));
+      const double2 t2 = cmul(w, O2);
+      const double2 X0 = cadd(E2, t2), X1 = csub(E2, t2);
+      const int sk = (ka << lg2) + k2, sp = (kb << lg2) + k2p;
+      const bool self = (rb == ra) && (k2p == k2);
+      if (MODE == 0) {
+        const double2 S0 = Sym[sk];
+        const double2 S1 = (k == 0) ? Sym[N] : cconj(Sym[sp]);
+        const double2 Y0 = cmul(S0, X0), Y1 = cmul(S1, X1);
+        const double2 Ep = cadd(Y0, Y1);
+        const double2 Op = cmulc(csub(Y0, Y1), w);
+        const double2 iOp = mul_i(Op);
+        ra[k2] = cadd(Ep, iOp);
+        if (!self) rb[k2p] = cconj(csub(Ep, iOp));
+      } else {
+        const double sc = 0.5 * scale;
+        Sout[sk] = cscale(X0, sc);
+        if (!self) Sout[sp] = cscale(cconj(X1), sc);
+        if (k == 0) Sout[N] = cscale(X1, sc);
+        if (sym_level >= 0) {
+          double2 sa, sb;
+          ab_symbols(A, ls, w, false, A.What[sk], sa, sb);
+          A.SA[sk] = sa;
+          A.SB[sk] = sb;
+          if (!self) {
+            const int kpf = (N - k) & (N - 1);
+            ab_symbols(A, ls, __ldg(tw + kpf), false, A.What[sp], sa, sb);
+            A.SA[sp] = sa;
+            A.SB[sp] = sb;
+          }
+          if (k == 0) {
+            ab_symbols(A, ls, __ldg(tw + N), true, A.What[N], sa, sb);
+            A.SA[N] = sa;
+            A.SB[N] = sb;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (MODE == 0) {
+      a = smem_fft<+1>(a, b, lg2, nl, tw, P.lgL);
+      for (int e = threadIdx.x; e < nl * N2; e += blockDim.x) {
+        const int line = e >> lg2, k2 = e & (N2 - 1);
+        const int it = i0 + (line >> 1);
+        const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
+        if ((line & 1) && row == it) continue;   // self-paired row stored once
+        A.Y2[(row << lg2) + k2] = a[e];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Row pass of the length-L complex plan (Bluestein): forward row FFT, then either multiply by
+// Tab (permuted) and inverse row FFT into Y2 (MODE 0) or store the spectrum * scale (MODE 1).
+// ------------------------------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const double2 *__restrict__ Tab,
+                                          double2 *__restrict__ Out, double scale) {
+  const CplxPlan &P = A.bp;
+  const int lg2 = P.lg2, N2 = P.N2;
+  int lo, hi;
+  my_items(P.N1, lo, hi);
+  for (int r0 = lo; r0 < hi; r0 += A.cap_brow) {
+    const int cnt = min(A.cap_brow, hi - r0);
+    double2 *a = S.a, *b = S.b;
+    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = A.Y1[(r0 << lg2) + e];
+    __syncthreads();
+    a = smem_fft<-1>(a, b, lg2, cnt, A.twL, A.cp.lgL);
+    b = (a == S.a) ? S.b : S.a;
+    if (MODE == 0) {
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = cmul(a[e], Tab[(r0 << lg2) + e]);
+      __syncthreads();
+      a = smem_fft<+1>(a, b, lg2, cnt, A.twL, A.cp.lgL);
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) A.Y2[(r0 << lg2) + e] = a[e];
+    } else {
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) Out[(r0 << lg2) + e] = cscale(a[e], scale);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// helpers on the level state
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double source_at(const Args &A, int j, int i) {
+  if (A.f_dense) return A.f_dense[(long long)j * A.n + i];
+  double s = 0.0;
+  for (int r = 0; r < A.src_rank; ++r) s += A.src_t[(long long)r * A.M + j] * A.src_x[(long long)r * A.n + i];
+  return s;
+}
+
+// eigenvalue of the level-j circulant preconditioner at n-frequency m (Eq. (3.7), diagonalised)
+__device__ __forceinline__ double2 lambda_p(const Args &A, const LevelScalars &s, int m) {
+  const double2 lw = A.LamW[m], lq = A.LamQ[m];
+  // q*lq + kp*lw + km*conj(lw)
+  const double re = s.q * lq.x + (s.kp + s.km) * lw.x;
+  const double im = s.q * lq.y + (s.kp - s.km) * lw.y;
+  return make_double2(s.eta - A.sigma * re, -A.sigma * im);
+}
+
+__device__ __forceinline__ void write_partials(const Args &A, const Smem &S, int rb, double (&acc)[3]) {
+  block_sum<3>(acc, S.red);
+  if (threadIdx.x == 0) {
+    double *p = A.partials + ((size_t)rb * gridDim.x + blockIdx.x) * 4;
+    p[0] = acc[0];
+    p[1] = acc[1];
+    p[2] = acc[2];
+  }
+}
+
+// Sum of all CTAs' partials of buffer rb, identical in every CTA (fixed order).
+__device__ __forceinline__ void read_partials(const Args &A, const Smem &S, int rb, double (&tot)[3]) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double *p = A.partials + ((size_t)rb * gridDim.x + b) * 4;
+    v[0] += p[0];
+    v[1] += p[1];
+    v[2] += p[2];
+  }
+  block_sum<3>(v, S.red);
+  tot[0] = v[0];
+  tot[1] = v[1];
+  tot[2] = v[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// phases
+// ------------------------------------------------------------------------------------------------
+
+// Bluestein, inverse n-point DFT of 1/Lambda_P (first column of P^{-1}), phase 1 of 3.
+__device__ void ph_pinv_b1(const Args &A, const Smem &S, int j) {
+  const LevelScalars s = level_scalars(A, j);
+  const int n = A.n;
+  col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 {
+                          if (m >= n) return make_double2(0.0, 0.0);
+                          const double2 lp = lambda_p(A, s, m);
+                          const double d = lp.x * lp.x + lp.y * lp.y;
+                          if (!(d > 0.0) || !isfinite(d)) raise_fatal(A, kESingular);
+                          const double2 inv = make_double2(lp.x / d, -lp.y / d);
+                          return cmul(inv, A.chirpI[m]);
+                        });
+}
+__device__ void ph_pinv_b2(const Args &A, const Smem &S) { crow_pass<0>(A, S, A.BhI, nullptr, 1.0); }
+__device__ void ph_pinv_b3(const Args &A, const Smem &S) {
+  const int n = A.n;
+  col_pass<true, false>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
+                        [&](int m, double2 z) -> double2 {
+                          if (m < n) A.cprime[m] = cmul(z, A.chirpI[m]).x;
+                          return z;
+                        });
+}
+// Toeplitz embedding of the circulant P^{-1} (entries t_d = c'_{d mod n}) and its column FFT.
+__device__ void ph_pinv_c1(const Args &A, const Smem &S) {
+  const int n = A.n, L = A.cp.L;
+  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 {
+                          double v[2];
+#pragma unroll
+                          for (int h = 0; h < 2; ++h) {
+                            const int i = 2 * m + h;
+                            v[h] = i < n ? A.cprime[i] : (i > L - n ? A.cprime[i + n - L] : 0.0);   // t_{-d} = c'_{n-d}
+                          }
+                          return make_double2(v[0], v[1]);
+                        });
+}
+// Spectrum of P^{-1}'s embedding, plus A and B of level j.
+__device__ void ph_pinv_c2(const Args &A, const Smem &S, int j) {
+  row_pass<1>(A, S, nullptr, A.SP, 1.0 / (4.0 * (double)A.cp.N), j);
+}
+// A and B spectra only (no preconditioner).
+__device__ void ph_ab_only(const Args &A, const Smem &S, int j) {
+  const LevelScalars s = level_scalars(A, j);
+  const ConvPlan &P = A.cp;
+  for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl <= P.N; sl += gridDim.x * blockDim.x) {
+    const int k = sl == P.N ? P.N : ((sl & (P.N2 - 1)) * P.N1 + (sl >> P.lg2));
+    double2 sa, sb;
+    ab_symbols(A, s, __ldg(A.twL + k), sl == P.N, A.What[sl], sa, sb);
+    A.SA[sl] = sa;
+    A.SB[sl] = sb;
+  }
+}
+
+// Commit of level j-1 (when commit), history sum of Lemma 1 for level j into H, contiguous.
+__device__ void ph_history(const Args &A, int j, bool commit) {
+  const int npair = (A.n + 1) >> 1;
+  const long long st = A.ring_stride;
+  const double2 *ring2 = reinterpret_cast<const double2 *>(A.ring);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
+    double2 dlast = make_double2(0.0, 0.0);
+    if (commit) {
+      const double2 xv = reinterpret_cast<const double2 *>(A.x)[t];
+      const double2 uv = reinterpret_cast<const double2 *>(A.u)[t];
+      dlast = make_double2(xv.x - uv.x, xv.y - uv.y);
+      reinterpret_cast<double2 *>(A.ring + (long long)(j - 1) * st)[t] = dlast;
+      reinterpret_cast<double2 *>(A.u)[t] = xv;
+    }
+    double hx = 0.0, hy = 0.0;
+    if (j >= 1) {
+      // s = 0 term: c^{(j)}_j = a_j - b_j; 1 <= s <= j-1: c^{(j)}_{j-s} = a + b - b (Lemma 1)
+      const int smax = commit ? j - 1 : j;   // levels read from the ring
+      int s = 0;
+      for (; s + 4 <= smax; s += 4) {
+        const double2 d0 = ring2[(s + 0) * (st >> 1) + t];
+        const double2 d1 = ring2[(s + 1) * (st >> 1) + t];
+        const double2 d2 = ring2[(s + 2) * (st >> 1) + t];
+        const double2 d3 = ring2[(s + 3) * (st >> 1) + t];
+        const double c0 = s == 0 ? A.hl[j] : A.hc[j - s];
+        const double c1 = A.hc[j - s - 1], c2 = A.hc[j - s - 2], c3 = A.hc[j - s - 3];
+        hx += c0 * d0.x; hy += c0 * d0.y;
+        hx += c1 * d1.x; hy += c1 * d1.y;
+        hx += c2 * d2.x; hy += c2 * d2.y;
+        hx += c3 * d3.x; hy += c3 * d3.y;
+      }
+      for (; s < smax; ++s) {
+        const double2 d = ring2[s * (st >> 1) + t];
+        const double c = s == 0 ? A.hl[j] : A.hc[j - s];
+        hx += c * d.x; hy += c * d.y;
+      }
+      if (commit) {   // s = j-1 from registers
+        const double c = (j - 1) == 0 ? A.hl[j] : A.hc[1];
+        hx += c * dlast.x; hy += c * dlast.y;
+      }
+    }
+    reinterpret_cast<double2 *>(A.H)[t] = make_double2(hx, hy);
+  }
+}
+
+// Final commit (end of a launch): d^j = x - u into the ring, u = x.
+__device__ void ph_commit(const Args &A, int j) {
+  const int npair = (A.n + 1) >> 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
+    const double2 xv = reinterpret_cast<const double2 *>(A.x)[t];
+    const double2 uv = reinterpret_cast<const double2 *>(A.u)[t];
+    reinterpret_cast<double2 *>(A.ring + (long long)j * A.ring_stride)[t] = make_double2(xv.x - uv.x, xv.y - uv.y);
+    reinterpret_cast<double2 *>(A.u)[t] = xv;
+  }
+}
+
+__device__ __forceinline__ double2 ld2(const double *v, int m) { return reinterpret_cast<const double2 *>(v)[m]; }
+__device__ __forceinline__ void st2(double *v, int m, double2 z) { reinterpret_cast<double2 *>(v)[m] = z; }
+
+// Symbols for level j (precondition or not).  Returns false if aborted.
+__device__ bool level_symbols(const Args &A, const Smem &S, int j) {
+  if (A.precond != 2) {
+    ph_pinv_b1(A, S, j);
+    if (!grid_sync(A)) return false;
+    ph_pinv_b2(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_b3(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_c1(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_c2(A, S, j);
+  } else {
+    ph_ab_only(A, S, j);
+  }
+  return grid_sync(A);
+}
+
+// ------------------------------------------------------------------------------------------------
+// the level kernel
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int j1) {
+  const Smem S = smem_view(lp_max_of(A));
+  const int n = A.n;
+  const bool pc = A.precond != 2;
+  int rb = 0;
+  for (int j = j0; j < j1; ++j) {
+    if (j == j0 || A.lv_newsym[j]) {
+      if (!level_symbols(A, S, j)) return;
+    }
+    // ---- RHS: g = B u^j - hscale * H^j + f^{j+sigma} (Eq. (3.1)) ----
+    const bool commit = j > j0;
+    ph_history(A, j, commit);
+    {
+      const double *src = commit ? A.x : A.u;
+      col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                            [&](int m, double2) -> double2 { return ld2(src, m); });
+    }
+    if (!grid_sync(A)) return;
+    row_pass<0>(A, S, A.SB, nullptr, 0.0, -1);
+    if (!grid_sync(A)) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                         [&](int m, double2 y) -> double2 {
+                           double gv[2] = {y.x, y.y};
+                           const double2 hv = ld2(A.H, m);
+                           const double hh[2] = {hv.x, hv.y};
+#pragma unroll
+                           for (int h = 0; h < 2; ++h) {
+                             const int i = 2 * m + h;
+                             if (i < n) {
+                               gv[h] = gv[h] - A.hscale * hh[h] + source_at(A, j, i);
+                               acc[0] += gv[h] * gv[h];
+                             } else {
+                               gv[h] = 0.0;
+                             }
+                           }
+                           const double2 g = make_double2(gv[0], gv[1]);
+                           st2(A.x, m, make_double2(0.0, 0.0));
+                           st2(A.r, m, g);
+                           st2(A.rt, m, g);
+                           st2(A.uu, m, g);
+                           st2(A.p, m, g);
+                           return g;
+                         });
+    write_partials(A, S, rb, acc);
+    if (!grid_sync(A)) return;
+    double tot[3];
+    read_partials(A, S, rb, tot);
+    rb ^= 1;
+    double rho = tot[0];
+    const double nr0 = sqrt(tot[0]);
+    int it = 0;
+    double rel = 0.0;
+    int lstat = kOK;
+    if (!(nr0 == nr0) || isinf(nr0)) lstat = kENonFinite;
+    bool first = true;
+    double beta = 0.0;
+    while (lstat == kOK && nr0 > 0.0) {
+      ++it;
+      if (!first) {
+        // u = r + beta q; p = u + beta (q + beta p); forward transform of p
+        col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                              [&](int m, double2) -> double2 {
+                                const double2 rv = ld2(A.r, m), qv = ld2(A.q, m), pv = ld2(A.p, m);
+                                const double2 uv = make_double2(rv.x + beta * qv.x, rv.y + beta * qv.y);
+                                const double2 pn = make_double2(uv.x + beta * (qv.x + beta * pv.x),
+                                                                uv.y + beta * (qv.y + beta * pv.y));
+                                st2(A.uu, m, uv);
+                                st2(A.p, m, pn);
+                                return pn;
+                              });
+        if (!grid_sync(A)) return;
+      }
+      first = false;
+      if (pc) {   // p^ = P^{-1} p
+        row_pass<0>(A, S, A.SP, nullptr, 0.0, -1);
+        if (!grid_sync(A)) return;
+        col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                             [&](int m, double2 z) -> double2 {
+                               if (2 * m >= n) z.x = 0.0;
+                               if (2 * m + 1 >= n) z.y = 0.0;
+                               return z;
+                             });
+        if (!grid_sync(A)) return;
+      }
+      // v^ = A p^, sigma = (r~, v^)
+      row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
+      if (!grid_sync(A)) return;
+      acc[0] = acc[1] = acc[2] = 0.0;
+      col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                            [&](int m, double2 z) -> double2 {
+                              if (2 * m >= n) z.x = 0.0;
+                              if (2 * m + 1 >= n) z.y = 0.0;
+                              st2(A.vh, m, z);
+                              const double2 rtv = ld2(A.rt, m);
+                              acc[0] += rtv.x * z.x + rtv.y * z.y;
+                              return z;
+                            });
+      write_partials(A, S, rb, acc);
+      if (!grid_sync(A)) return;
+      read_partials(A, S, rb, tot);
+      rb ^= 1;
+      const double sig = tot[0];
+      if (sig == 0.0) { lstat = kEBreakdown; break; }
+      if (!(sig == sig) || isinf(sig)) { lstat = kENonFinite; break; }
+      const double alpha = rho / sig;
+      // q = u - alpha v^; w = u + q; forward transform of w (x += alpha w when unpreconditioned)
+      col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                            [&](int m, double2) -> double2 {
+                              const double2 uv = ld2(A.uu, m), vv = ld2(A.vh, m);
+                              const double2 qv = make_double2(uv.x - alpha * vv.x, uv.y - alpha * vv.y);
+                              const double2 wv = make_double2(uv.x + qv.x, uv.y + qv.y);
+                              st2(A.q, m, qv);
+                              if (!pc) {
+                                const double2 xv = ld2(A.x, m);
+                                st2(A.x, m, make_double2(xv.x + alpha * wv.x, xv.y + alpha * wv.y));
+                              }
+                              return wv;
+                            });
+      if (!grid_sync(A)) return;
+      if (pc) {   // u^ = P^{-1} w; x += alpha u^
+        row_pass<0>(A, S, A.SP, nullptr, 0.0, -1);
+        if (!grid_sync(A)) return;
+        col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                             [&](int m, double2 z) -> double2 {
+                               if (2 * m >= n) z.x = 0.0;
+                               if (2 * m + 1 >= n) z.y = 0.0;
+                               const double2 xv = ld2(A.x, m);
+                               st2(A.x, m, make_double2(xv.x + alpha * z.x, xv.y + alpha * z.y));
+                               return z;
+                             });
+        if (!grid_sync(A)) return;
+      }
+      // r -= alpha A u^; rho' = (r~, r), ||r||^2
+      row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
+      if (!grid_sync(A)) return;
+      acc[0] = acc[1] = acc[2] = 0.0;
+      col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                            [&](int m, double2 z) -> double2 {
+                              if (2 * m >= n) z.x = 0.0;
+                              if (2 * m + 1 >= n) z.y = 0.0;
+                              const double2 rv = ld2(A.r, m), rtv = ld2(A.rt, m);
+                              const double2 rn = make_double2(rv.x - alpha * z.x, rv.y - alpha * z.y);
+                              st2(A.r, m, rn);
+                              acc[0] += rtv.x * rn.x + rtv.y * rn.y;
+                              acc[1] += rn.x * rn.x + rn.y * rn.y;
+                              return z;
+                            });
+      write_partials(A, S, rb, acc);
+      if (!grid_sync(A)) return;
+      read_partials(A, S, rb, tot);
+      rb ^= 1;
+      rel = sqrt(tot[1]) / nr0;
+      if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
+      if (rel < A.tol) break;
+      if (it >= A.maxit) { lstat = kENotConverged; break; }
+      if (tot[0] == 0.0) { lstat = kEBreakdown; break; }
+      beta = tot[0] / rho;
+      rho = tot[0];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      A.iters[j] = it;
+      A.resid[j] = rel;
+      if (lstat != kOK) {
+        atomicCAS(A.status, 0, lstat);
+        if (lstat != kENotConverged) atomicExch(A.status + 1, 1);
+      }
+    }
+    if (lstat != kOK && lstat != kENotConverged) return;   // consistent in every CTA
+  }
+  if (!grid_sync(A)) return;
+  ph_commit(A, j1 - 1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}); x and y are padded device vectors.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int j, const double *xin, double *yout) {
+  const Smem S = smem_view(lp_max_of(A));
+  const int n = A.n;
+  if (!level_symbols(A, S, j)) return;
+  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 { return ld2(xin, m); });
+  if (!grid_sync(A)) return;
+  row_pass<0>(A, S, op == 0 ? A.SA : (op == 1 ? A.SB : A.SP), nullptr, 0.0, -1);
+  if (!grid_sync(A)) return;
+  col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                        [&](int m, double2 z) -> double2 {
+                          if (2 * m >= n) z.x = 0.0;
+                          if (2 * m + 1 >= n) z.y = 0.0;
+                          st2(yout, m, z);
+                          return z;
+                        });
+}
+
+// ------------------------------------------------------------------------------------------------
+// setup: tables, spectrum of W's embedding, Bluestein kernels, eigenvalues of s(W), s(Q)
+// ------------------------------------------------------------------------------------------------
+struct SetupArgs {
+  const double *omega;   // WSGD weights omega_0..omega_{n+1}
+  double2 *What, *LamW, *LamQ, *BhI, *BhF, *chirpI, *twL;
+  int precond;
+};
+
+// Entry t_d of the Toeplitz matrix (0: W_beta, 1: Q), d in (-n, n).
+__device__ __forceinline__ double toe_entry(const double *omega, int which, int d) {
+  if (which == 0) return d >= -1 ? omega[d + 1] : 0.0;
+  return d == 1 ? -1.0 : (d == -1 ? 1.0 : 0.0);
+}
+// First column of the circulant approximation (Strang: central diagonals; T. Chan: optimal).
+__device__ __forceinline__ double circ_col(const double *omega, int which, int kind, int n, int k) {
+  if (k == 0) return toe_entry(omega, which, 0);
+  if (kind == 1) return ((double)(n - k) * toe_entry(omega, which, k) + (double)k * toe_entry(omega, which, k - n)) / (double)n;
+  return k <= n / 2 ? toe_entry(omega, which, k) : toe_entry(omega, which, k - n);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T) {
+  const Smem S = smem_view(lp_max_of(A));
+  const int n = A.n, L = A.cp.L;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // tables: twiddles e^{-2 pi i k/L}, chirp e^{i pi (k^2 mod 2n)/n}
+  for (int k = gt; k < L; k += gs) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    T.twL[k] = make_double2(c, s);
+  }
+  for (int k = gt; k < n; k += gs) {
+    const long long k2 = ((long long)k * (long long)k) % (2ll * n);
+    double s, c;
+    sincospi((double)k2 / (double)n, &s, &c);
+    T.chirpI[k] = make_double2(c, s);
+  }
+  if (!grid_sync(A)) return;
+  // spectrum of the L-embedding of W_beta: t_0 = omega_1 ... t_{n-1} = omega_n, t_{-1} = omega_0
+  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 {
+                          double v[2];
+#pragma unroll
+                          for (int h = 0; h < 2; ++h) {
+                            const int i = 2 * m + h;
+                            v[h] = i < n ? T.omega[i + 1] : (i == L - 1 ? T.omega[0] : 0.0);
+                          }
+                          return make_double2(v[0], v[1]);
+                        });
+  if (!grid_sync(A)) return;
+  row_pass<1>(A, S, nullptr, T.What, 1.0, -1);
+  if (!grid_sync(A)) return;
+  // Bluestein kernels: b_d = e^{-+ i pi d^2/n} placed circularly (|d| < n), spectra scaled for
+  // the inverse (1/(L n)) and forward (1/L) n-point DFTs.
+  for (int pass = 0; pass < 2; ++pass) {
+    col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                          [&](int m, double2) -> double2 {
+                            int d = m < n ? m : (m > L - n ? L - m : -1);
+                            if (d < 0) return make_double2(0.0, 0.0);
+                            const double2 c = T.chirpI[d];
+                            return pass == 0 ? cconj(c) : c;
+                          });
+    if (!grid_sync(A)) return;
+    crow_pass<1>(A, S, nullptr, pass == 0 ? T.BhI : T.BhF,
+                 pass == 0 ? 1.0 / ((double)L * (double)n) : 1.0 / (double)L);
+    if (!grid_sync(A)) return;
+  }
+  // eigenvalues of s(W_beta) and s(Q): forward n-point DFT by Bluestein
+  for (int which = 0; which < 2; ++which) {
+    col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                          [&](int m, double2) -> double2 {
+                            if (m >= n) return make_double2(0.0, 0.0);
+                            const double c = circ_col(T.omega, which, T.precond, n, m);
+                            return cscale(cconj(T.chirpI[m]), c);
+                          });
+    if (!grid_sync(A)) return;
+    // reuse crow_pass<0> with the forward kernel
+    {
+      Args B = A;
+      B.BhI = T.BhF;
+      crow_pass<0>(B, S, T.BhF, nullptr, 1.0);
+    }
+    if (!grid_sync(A)) return;
+    double2 *out = which == 0 ? T.LamW : T.LamQ;
+    col_pass<true, false>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
+                          [&](int m, double2 z) -> double2 {
+                            if (m < n) out[m] = cmulc(z, T.chirpI[m]);
+                            return z;
+                          });
+    if (!grid_sync(A)) return;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// weights and per-level tables (Lemma 1, Lemma 2)
+// ------------------------------------------------------------------------------------------------
+// omega_k for k = 0..n+1: Grunwald recurrence g_k = (1 - (beta+1)/k) g_{k-1} (Lemma 3) run by
+// one thread with explicit rounding (no contraction), then the WSGD combination (Lemma 2).
+__global__ void grunwald_kernel(double *g, int K, double beta) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double gk = 1.0;
+    g[0] = gk;
+    for (int k = 1; k <= K; ++k) {
+      const double f = __dadd_rn(1.0, -__ddiv_rn(beta + 1.0, (double)k));
+      gk = __dmul_rn(f, gk);
+      g[k] = gk;
+    }
+  }
+}
+
+__global__ void wsgd_kernel(const double *g, double *omega, int K, double beta) {
+  const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
+  const double lam0 = (4.0 - beta * beta) / 6.0;
+  const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+    double w = __dmul_rn(lam1, g[k]);
+    if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, g[k - 1]));
+    if (k >= 2) w = __dadd_rn(w, __dmul_rn(lamm1, g[k - 2]));
+    omega[k] = w;
+  }
+}
+
+// a_l, b_l of Lemma 1 and the history coefficients hc[m] = a_m + b_{m+1} - b_m, hl[j] = a_j - b_j;
+// per level eta_j = c^{(j)}_0 / (tau^alpha Gamma(2-alpha)) and the scaled coefficients.
+__device__ __forceinline__ double l21_a(double alpha, double sigma, int l) {
+  if (l == 0) return pow(sigma, 1.0 - alpha);
+  return pow(l + sigma, 1.0 - alpha) - pow(l - 1 + sigma, 1.0 - alpha);
+}
+__device__ __forceinline__ double l21_b(double alpha, double sigma, int l) {
+  if (l == 0) return 0.0;
+  return (pow(l + sigma, 2.0 - alpha) - pow(l - 1 + sigma, 2.0 - alpha)) / (2.0 - alpha) -
+         0.5 * (pow(l + sigma, 1.0 - alpha) + pow(l - 1 + sigma, 1.0 - alpha));
+}
+
+__global__ void time_tables_kernel(int M, double alpha, double tau, double h, double beta,
+                                   const double *gam, const double *dp, const double *dm,
+                                   double *hc, double *hl, double *eta, double *q, double *kp,
+                                   double *km) {
+  const double sigma = 1.0 - alpha / 2.0;
+  const double denom = pow(tau, alpha) * tgamma(2.0 - alpha);
+  const double hb = pow(h, beta);
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= M; l += gridDim.x * blockDim.x) {
+    const double al = l21_a(alpha, sigma, l), bl = l21_b(alpha, sigma, l);
+    hl[l] = al - bl;
+    hc[l] = l >= 1 ? al + l21_b(alpha, sigma, l + 1) - bl : 0.0;
+    if (l < M) {
+      const double c0 = l == 0 ? l21_a(alpha, sigma, 0) : l21_a(alpha, sigma, 0) + l21_b(alpha, sigma, 1);
+      eta[l] = c0 / denom;
+      q[l] = gam[l] / (2.0 * h);
+      kp[l] = dp[l] / hb;
+      km[l] = dm[l] / hb;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+static int coop_launch(const void *fn, int grid, size_t smem, cudaStream_t st, void **args) {
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, st);
+  return e == cudaSuccess ? kOK : kECuda;
+}
+
+size_t level_smem_bytes(const Args &A) {
+  int m = A.cap_col << A.cp.lg1;
+  m = m > ((2 * A.cap_row) << A.cp.lg2) ? m : ((2 * A.cap_row) << A.cp.lg2);
+  m = m > (A.cap_bcol << A.bp.lg1) ? m : (A.cap_bcol << A.bp.lg1);
+  m = m > (A.cap_brow << A.bp.lg2) ? m : (A.cap_brow << A.bp.lg2);
+  return (size_t)2 * m * sizeof(double2) + 4 * 32 * sizeof(double);
+}
+
+const void *level_kernel_ptr() { return (const void *)level_kernel; }
+const void *apply_kernel_ptr() { return (const void *)apply_kernel; }
+const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
+
+int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1) {
+  Args a = A;
+  void *args[] = {&a, &j0, &j1};
+  return coop_launch((const void *)level_kernel, grid, smem, st, args);
+}
+
+int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
+                 const double *xin, double *yout) {
+  Args a = A;
+  void *args[] = {&a, &op, &j, &xin, &yout};
+  return coop_launch((const void *)apply_kernel, grid, smem, st, args);
+}
+
+int launch_setup_tables(const Args &A, int grid, size_t smem, cudaStream_t st, const SetupArgs &T) {
+  Args a = A;
+  SetupArgs t = T;
+  void *args[] = {&a, &t};
+  return coop_launch((const void *)setup_kernel, grid, smem, st, args);
+}
+
+int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const double *omega,
+                 double2 *What, double2 *LamW, double2 *LamQ, double2 *BhI, double2 *BhF,
+                 double2 *chirpI, double2 *twL, double beta, int precond) {
+  (void)beta;
+  SetupArgs T;
+  T.omega = omega;
+  T.What = What;
+  T.LamW = LamW;
+  T.LamQ = LamQ;
+  T.BhI = BhI;
+  T.BhF = BhF;
+  T.chirpI = chirpI;
+  T.twL = twL;
+  T.precond = precond;
+  return launch_setup_tables(A, grid, smem, st, T);
+}
+
+int launch_weights(double *omega, double *g_tmp, int n, double beta, cudaStream_t st) {
+  grunwald_kernel<<<1, 32, 0, st>>>(g_tmp, n + 1, beta);
+  wsgd_kernel<<<(n + 2 + kThreads - 1) / kThreads, kThreads, 0, st>>>(g_tmp, omega, n + 1, beta);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+}
+
+int launch_time_tables(int M, double alpha, double tau, double h, double beta, const double *gam,
+                       const double *dp, const double *dm, double *hc, double *hl, double *eta,
+                       double *q, double *kp, double *km, cudaStream_t st) {
+  time_tables_kernel<<<(M + 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+      M, alpha, tau, h, beta, gam, dp, dm, hc, hl, eta, q, kp, km);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+}
+
+}  // namespace tsf

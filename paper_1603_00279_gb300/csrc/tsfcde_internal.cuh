@@ -1,0 +1,263 @@
+// Internal declarations shared by the translation units of libtsfcde (not part of the C ABI).
+//
+// Data layout in device memory (one context = one TSFCDE instance):
+//   * real vectors of the level solve (u, x, r, r~, p, q, u_cgs, v^, H) hold n values followed by
+//     zeros up to L = max(8, 2^ceil(log2 2n)), the length of the circulant embedding of an n x n
+//     Toeplitz matrix (Section 3.2: "B u^j can be evaluated by FFTs"); viewed as L/2 complex
+//     numbers z_m = (v_{2m}, v_{2m+1}) they feed a half-length complex FFT (real-input trick);
+//   * FFTs of length N = L/2 are split N = N1 x N2 (four-step): "column" items are the N2
+//     strided lines of N1 points, "row" items are the N1 contiguous lines of N2 points.  Spectra
+//     of Toeplitz kernels are stored in the permuted order slot(k) = (k mod N1) N2 + k / N1
+//     produced by the row pass, plus the Nyquist value at slot N;
+//   * the Bluestein transforms (n-point DFTs of the circulant columns, Eq. (3.7) and the
+//     diagonalisation below it) use complex FFTs of length L split L = Nb1 x Nb2 the same way;
+//   * the history ring holds d^s = u^{s+1} - u^s for every committed level s, level-major with a
+//     256-byte aligned stride, FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsf {
+
+constexpr int kThreads = 256;                 // threads per CTA of every kernel
+constexpr long long kSpinLimit = 1ll << 23;   // bound on a barrier wait (about 2-4 s)
+
+// status codes (mirror include/tsfcde.h)
+constexpr int kOK = 0, kEInvalid = 1, kENoMem = 2, kECuda = 3, kENonFinite = 4,
+              kENotConverged = 5, kEBreakdown = 6, kESingular = 7, kETimeout = 8, kEState = 9;
+
+struct ConvPlan {  // real length L, complex length N = L/2 = N1 * N2
+  int L, lgL, N, lgN, N1, lg1, N2, lg2;
+};
+struct CplxPlan {  // complex length Nc = L = N1 * N2
+  int Nc, lgNc, N1, lg1, N2, lg2;
+};
+
+// Everything a device kernel needs, passed by value.
+struct Args {
+  int n, M;
+  ConvPlan cp;
+  CplxPlan bp;
+  int precond;          // 0 Strang, 1 T. Chan, 2 none
+  double sigma, hscale; // sigma = 1 - alpha/2, hscale = tau^-alpha / Gamma(2-alpha)
+  double tol;
+  int maxit;
+  int cap_col, cap_row, cap_bcol, cap_brow;   // lines per CTA chunk in each phase kind
+  // tables
+  const double2 *twL;     // e^{-2 pi i k / L}, k < L
+  const double2 *What;    // spectrum of the L-embedding of W_beta, permuted, N+1
+  const double2 *LamW;    // n-point DFT of the circulant column s(W_beta), n
+  const double2 *LamQ;    // n-point DFT of the circulant column s(Q), n
+  const double2 *BhI;     // Bluestein kernel spectrum for the inverse n-DFT, permuted, L
+  const double2 *chirpI;  // e^{+i pi k^2 / n}, k < n
+  const double *lv_eta, *lv_q, *lv_kp, *lv_km;  // per level: eta_j, gamma/(2h), d+/h^b, d-/h^b
+  const int *lv_newsym;   // per level: 1 if the level operators differ from the previous level
+  const double *hc;       // hc[m] = a_m + b_{m+1} - b_m, m >= 1 (Lemma 1)
+  const double *hl;       // hl[j] = a_j - b_j (Lemma 1, m = j)
+  int src_rank;
+  const double *src_x;    // src_rank x n
+  const double *src_t;    // src_rank x M
+  const double *f_dense;  // M x n or null
+  // state
+  double *u, *x, *r, *rt, *p, *q, *uu, *vh, *H;
+  double *ring;
+  long long ring_stride;
+  double2 *SA, *SB, *SP;  // per-level spectra (permuted, N+1), scaled by 1/(4N)
+  double2 *Y1, *Y2;       // FFT work, L complex each
+  double *cprime;         // first column of P^{-1}, n
+  double *partials;       // 2 x gridDim x 4
+  unsigned *bar;          // [0] arrival count, [32] generation
+  int *status;            // [0] status, [1] abort flag
+  int *iters;             // M
+  double *resid;          // M
+};
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 mul_i(double2 a) { return make_double2(-a.y, a.x); }     // * i
+__device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }    // * -i
+
+// ---------------------------------------------------------------------------------------------
+// Stockham radix-4/2 FFT of `nl` lines of length P = 2^lgP in shared memory.
+// Line l occupies a[l*P .. l*P+P); b is a scratch area of the same size.  SIGN = -1 forward,
+// +1 inverse (unnormalised).  Twiddles come from tw[k] = e^{-2 pi i k / 2^lgT}, 2^lgT >= P.
+// All threads of the CTA take part; returns the buffer holding the result.
+// Stage with current sub-length Ls and radix r: for j < P/r, k = j mod Ls, a_q = x[j + q P/r]
+// is twiddled by e^{SIGN 2 pi i q k/(r Ls)}, an r-point DFT is taken, and output q goes to
+// y[(j - k) r + k + q Ls].
+// ---------------------------------------------------------------------------------------------
+template <int SIGN>
+__device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, int nl,
+                                             const double2 *__restrict__ tw, int lgT) {
+  const int P = 1 << lgP;
+  int lgLs = 0;
+  while (lgLs < lgP) {
+    const int Ls = 1 << lgLs;
+    if (lgP - lgLs >= 2) {
+      const int Q = P >> 2;
+      const int nb = nl * Q;
+      const int sh = lgT - lgLs - 2;
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const int l = t >> (lgP - 2);
+        const int j = t & (Q - 1);
+        const int k = j & (Ls - 1);
+        const double2 *x = a + l * P;
+        double2 *y = b + l * P;
+        double2 a0 = x[j], a1 = x[j + Q], a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
+        if (k) {
+          double2 w1 = __ldg(tw + ((k) << sh));
+          double2 w2 = __ldg(tw + ((2 * k) << sh));
+          double2 w3 = __ldg(tw + ((3 * k) << sh));
+          if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
+          a1 = cmul(a1, w1);
+          a2 = cmul(a2, w2);
+          a3 = cmul(a3, w3);
+        }
+        const double2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+        const double2 b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
+        const int base = ((j - k) << 2) + k;
+        y[base] = cadd(b0, b2);
+        y[base + Ls] = cadd(b1, b3);
+        y[base + 2 * Ls] = csub(b0, b2);
+        y[base + 3 * Ls] = csub(b1, b3);
+      }
+      lgLs += 2;
+    } else {
+      const int Q = P >> 1;
+      const int nb = nl * Q;
+      const int sh = lgT - lgLs - 1;
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const int l = t >> (lgP - 1);
+        const int j = t & (Q - 1);
+        const int k = j & (Ls - 1);
+        const double2 *x = a + l * P;
+        double2 *y = b + l * P;
+        double2 a0 = x[j], a1 = x[j + Q];
+        if (k) {
+          double2 w1 = __ldg(tw + (k << sh));
+          if (SIGN > 0) w1 = cconj(w1);
+          a1 = cmul(a1, w1);
+        }
+        const int base = ((j - k) << 1) + k;
+        y[base] = cadd(a0, a1);
+        y[base + Ls] = csub(a0, a1);
+      }
+      lgLs += 1;
+    }
+    __syncthreads();
+    double2 *t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------------------------
+// memory-order helpers and the bounded device-wide barrier
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
+
+// Sets a fatal status (first one wins) and raises the abort flag.
+__device__ __forceinline__ void raise_fatal(const Args &A, int code) {
+  atomicCAS(A.status, 0, code);
+  atomicExch(A.status + 1, 1);
+  __threadfence();
+}
+
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after kSpinLimit polls the
+// CTA records E_TIMEOUT, raises the abort flag and leaves.  Returns false when the kernel must
+// stop (abort raised anywhere); all CTAs then return without touching the barrier again.
+__device__ __forceinline__ bool grid_sync(const Args &A) {
+  __shared__ int s_go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned *count = A.bar;
+    unsigned *gen = A.bar + 32;
+    const unsigned g = ld_acquire_u32(gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      st_release_u32(gen, g + 1);
+    } else {
+      long long spins = 0;
+      while (ld_acquire_u32(gen) == g) {
+        if (++spins > kSpinLimit) {
+          raise_fatal(A, kETimeout);
+          break;
+        }
+        if ((spins & 255) == 0 && ld_volatile_i32(A.status + 1)) break;
+      }
+    }
+    __threadfence();
+    s_go = ld_volatile_i32(A.status + 1) == 0;
+  }
+  __syncthreads();
+  return s_go != 0;
+}
+
+// Deterministic block reduction of K values (fixed shuffle tree, fixed warp order).
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *sm /* K*32 doubles */) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[k] = x;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k * 32 + w] = v[k];
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sm[k * 32 + i];
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+// Host-side entry points implemented in level_kernels.cu.
+int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
+int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
+                 const double *xin, double *yout);
+int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const double *omega,
+                 double2 *What, double2 *LamW, double2 *LamQ, double2 *BhI, double2 *BhF,
+                 double2 *chirpI, double2 *twL, double beta, int precond);
+int launch_weights(double *omega, double *g_tmp, int n, double beta, cudaStream_t st);
+int launch_time_tables(int M, double alpha, double tau, double h, double beta, const double *gam,
+                       const double *dp, const double *dm, double *hc, double *hl, double *eta,
+                       double *q, double *kp, double *km, cudaStream_t st);
+size_t level_smem_bytes(const Args &A);
+const void *level_kernel_ptr();
+const void *apply_kernel_ptr();
+const void *setup_kernel_ptr();
+
+}  // namespace tsf

@@ -1,0 +1,139 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 relative L2 gap <= 1e-10 per level on instances where u64 * kappa_eff is far
+below 1e-10 (n <= ~1000); operator products (A x, B x, P^{-1} x) to 1e-12 relative to
+||op|| ||x||, the rounding of two FFTs of length L in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import tsfcde_workloads as W
+from gpu_common import rel_l2, solver_module
+
+pytestmark = pytest.mark.gpu
+
+
+def _march_all_levels(P, prob, **kw):
+    s = P.Solver.from_problem(prob, **kw)
+    levels = [s.get_level()[0]]
+    for _ in range(prob.M):
+        s.step(1)
+        levels.append(s.get_level()[0])
+    it, rs = s.history(prob.M)
+    s.close()
+    return levels, it, rs
+
+
+@pytest.mark.parametrize("precond", ["strang", "tchan"])
+def test_small_config_every_level(precond):
+    """n=127, M=64, alpha=0.6, beta=1.7: every level against dense GE, gap <= 1e-10."""
+    P = solver_module()
+    prob = W.config_small(preconditioner=precond)
+    ref = O.run(prob)
+    got, it, rs = _march_all_levels(P, prob)
+    gaps = [rel_l2(got[j], ref[j]) for j in range(prob.M + 1)]
+    assert max(gaps) <= 1e-10, max(gaps)
+    assert np.all(rs < 1e-12) and np.all(it > 0)
+
+
+def test_small_config_one_launch_equals_stepwise():
+    """All levels in one launch (commit fused into the next level) == one launch per level."""
+    P = solver_module()
+    prob = W.config_small()
+    s = P.Solver.from_problem(prob)
+    u_all = s.solve()
+    s.reset()
+    for _ in range(prob.M):
+        s.step(1)
+    u_step = s.get_level()[0]
+    s.close()
+    assert rel_l2(u_all, u_step) < 1e-13
+    ref = O.run(prob)[-1]
+    assert rel_l2(u_all, ref) < 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 31, 100, 257, 1000])
+@pytest.mark.parametrize("precond", ["strang", "tchan"])
+def test_operator_products(n, precond):
+    """y = A x, B x, P^{-1} x at several levels against dense matrices, ragged n included."""
+    P = solver_module()
+    prob = W.example2(n, 16, 0.7, 1.45)
+    prob.preconditioner = precond
+    s = P.Solver.from_problem(prob)
+    rng = np.random.default_rng(n)
+    for j in (0, 1, 9):
+        A, B = O.level_matrices(prob, j)
+        Pm = O.preconditioner_matrix(prob, j, precond)
+        x = rng.standard_normal(n)
+        for op, ref in (("A", A @ x), ("B", B @ x), ("Pinv", np.linalg.solve(Pm, x))):
+            y = s.apply(op, j, x)
+            mat = {"A": A, "B": B, "Pinv": np.linalg.inv(Pm)}[op]
+            scale = np.linalg.norm(mat, 2) * np.linalg.norm(x)
+            assert np.linalg.norm(y - ref) <= 1e-12 * scale, (op, j, np.linalg.norm(y - ref) / scale)
+    s.close()
+
+
+@pytest.mark.parametrize("n,M", [(1, 3), (2, 5), (3, 1), (8, 4), (33, 20), (500, 30)])
+def test_ragged_and_tiny_marches(n, M):
+    P = solver_module()
+    prob = W.example2(n, M, 0.55, 1.6)
+    ref = O.run(prob)
+    got, it, rs = _march_all_levels(P, prob)
+    assert max(rel_l2(got[j], ref[j]) for j in range(M + 1)) <= 1e-10
+
+
+def test_example1_iterations_and_tables():
+    """Paper Example 1 at N = M = 128 (n = 127): 6-10 CGS iterations per level (Section 3.2)
+    and the Table 1 error 1.6010e-5 (alpha = 0.1, beta = 1.8)."""
+    P = solver_module()
+    prob = W.example1(127, 128, 0.1, 1.8)
+    s = P.Solver.from_problem(prob)
+    levels = [s.get_level()[0]]
+    for _ in range(prob.M):
+        s.step(1)
+        levels.append(s.get_level()[0])
+    it, _ = s.history(prob.M)
+    s.close()
+    e2, em = O.errors_vs_exact(prob, levels)
+    assert abs(e2 / 1.6010e-5 - 1) < 0.005 and abs(em / 2.3815e-5 - 1) < 0.005
+    assert 6 <= it.min() and it.max() <= 10, (it.min(), it.max())
+
+
+def test_separable_source_equals_callback():
+    P = solver_module()
+    prob = W.config_small(n=255, M=32)
+    s1 = P.Solver.from_problem(prob, source="callback")
+    s2 = P.Solver.from_problem(prob, source="separable")
+    u1, u2 = s1.solve(), s2.solve()
+    s1.close()
+    s2.close()
+    assert rel_l2(u1, u2) < 1e-12
+
+
+def test_unpreconditioned_matches():
+    """Plain CGS (no preconditioner): its recursively updated residual drifts away from the true
+    one; the oracle's own dense CGS on these systems ends 4e-9 .. 3e-7 away from GE, so the
+    bound here is 1e-5 rather than the preconditioned 1e-10."""
+    P = solver_module()
+    prob = W.config_small(n=63, M=8, preconditioner="none")
+    ref = O.run(prob)
+    got, it, _ = _march_all_levels(P, prob)
+    assert max(rel_l2(got[j], ref[j]) for j in range(prob.M + 1)) <= 1e-5
+    assert np.all(it > 20)
+
+
+def test_large_config_proxy_first_levels():
+    """alpha=0.3, beta=1.9 with the large instance's coefficients at n=1023 (u64*kappa_eff
+    ~ 4e-11): first 8 levels against dense GE."""
+    P = solver_module()
+    prob = W.config_large(n=1023, M=1024, preconditioner="tchan")
+    ref = O.run(prob, levels=8)
+    s = P.Solver.from_problem(prob, source="separable")
+    for j in range(8):
+        s.step(1)
+        got = s.get_level()[0]
+        assert rel_l2(got, ref[j + 1]) <= 1e-10, (j, rel_l2(got, ref[j + 1]))
+    s.close()
