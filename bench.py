@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput of the TSFCDE time march on GB300: grid-point updates per second (n * M / s).
+
+A step is one whole time march of the workload (all M levels: history sum, FFT Toeplitz
+products, circulant-preconditioned CGS per level) from u^0, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload large|small|mixed] [--precond tchan|strang|none]
+
+Default workload: n = 2^16-1 interior points, M = 1024 levels, alpha = 0.3, beta = 1.9,
+gamma = 0.5, d+ = 1+t, d- = 1-t/2, u = (t^2+1) x^2 (1-x)^2, T. Chan preconditioner, tol 1e-12,
+FP64.  Multi-GPU (torchrun): independent replicas, one per rank (the march is sequential in
+time and a single instance does not shard), weak scaling, max time over ranks.
+
+--impl reference times the FP64 CPU oracle (dense Gaussian elimination per level) on the host
+cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tsfcde_workloads as W  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 flop x max clock
+
+
+def workload(name: str, precond):
+    if name == "large":
+        p = W.config_large()
+    elif name == "small":
+        p = W.config_small()
+    elif name == "mixed":
+        p = W.config_mixed()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if precond:
+        p.preconditioner = precond
+    return p
+
+
+def describe(p) -> dict:
+    return {"workload": f"tsfcde_{p.name}", "n": p.n, "M": p.M, "alpha": p.alpha, "beta": p.beta,
+            "preconditioner": p.preconditioner, "tol": p.tol, "source": "separable(4)",
+            "updates_per_step": p.n * p.M}
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic work of one march (FFT flops by the 5 N log2 N convention for a complex FFT of
+# length N; a real-input transform of length L counts 2.5 L log2 L)
+# ---------------------------------------------------------------------------------------------
+def algorithmic_flops(p, iters: np.ndarray, newsym_levels: int) -> float:
+    n, M = p.n, p.M
+    L = max(8, 1 << math.ceil(math.log2(2 * n)))
+    lg = math.log2(L)
+    conv = 5.0 * L * lg + 3.0 * L
+    pc = p.preconditioner != "none"
+    convs = M + (4 if pc else 2) * float(iters.sum())
+    sym = (12.5 * L * lg + 24.0 * n) if pc else 0.0
+    hist = 2.0 * n * (M * (M - 1) / 2.0)
+    vec = 19.0 * n * float(iters.sum()) + 12.0 * n * M
+    return conv * convs + sym * newsym_levels + hist + vec
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(p, budget_s: float = 15.0):
+    """Time the oracle (dense GE per level) on the workload's parameters at a reduced n, for as
+    many levels as fit the budget; returns (updates/s, description, cores)."""
+    import oracle as O
+    n_s = min(p.n, 2047)
+    cls = {"large": W.config_large, "small": W.config_small, "mixed": W.config_mixed}[p.name]
+    q = cls(n=n_s, M=p.M)
+    q.preconditioner = p.preconditioner
+    t0 = time.perf_counter()
+    levels = 1
+    O.run(q, levels=1)
+    dt = time.perf_counter() - t0
+    if dt < budget_s / 4:
+        levels = max(2, min(p.M, int(budget_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        O.run(q, levels=levels)
+        dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    desc = (f"oracle (dense LU per level, numpy/LAPACK) on the workload's alpha, beta and "
+            f"coefficients at n={n_s} (workload n={p.n}), levels 0..{levels - 1} of M={p.M}; "
+            f"{dt:.1f} s; dense LU costs grow as n^3 per level, so at the workload's n the "
+            f"oracle is ~{(p.n / n_s) ** 2:.0f}x slower per update than this sample")
+    return n_s * levels / dt, desc, cores, dt
+
+
+def run_reference(args, p):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals, descs = [], []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(p, budget_s=2.0)
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, d, cores, dt = oracle_sample(p, budget_s=20.0)
+        vals.append(v)
+        t_all += dt
+        descs.append(d)
+    v = float(np.mean(vals))
+    line = {"metric": "grid-point updates/s", "value": v, "unit": "updates/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution)",
+            "config": describe(p),
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": descs[-1]},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------------------------
+def run_native(args, p):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1603_00279_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1603_00279_gb300 as P
+
+    stream = torch.cuda.Stream()
+    s = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
+                              maxit=args.maxit)
+    n, M = p.n, p.M
+
+    def one_step():
+        s.reset()
+        return s.step(M)
+
+    for _ in range(args.warmup):
+        one_step()
+    it, _ = s.history(M)
+    # timed region: device-resident inputs
+    stats = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(one_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * M * args.steps / (ms_max / 1e3)
+    it, res = s.history(M)
+    launches = int(sum(st["device_launches"] for st in stats))
+    kernel_ms = float(np.mean([st["device_ms"] for st in stats]))
+    newsym = M if p.name != "batch" else 2
+    flops = algorithmic_flops(p, it, newsym)
+    achieved = flops / (kernel_ms / 1e3) / 1e12
+
+    # end to end through the C ABI with pinned host buffers: H2D of u^0, D2H of u^M per step
+    u0 = torch.from_numpy(np.ascontiguousarray(p.phi(p.grid()))).pin_memory()
+    uM = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.reset(u0_ptr=u0.data_ptr())
+        s.solve(out_ptr=uM.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_val = world * n * M / float(tt.item())
+
+    # accuracy of the march against the manufactured solution (a property at any size)
+    u_end = uM.numpy()
+    err = float(np.sqrt(p.h) * np.linalg.norm(u_end - p.exact(p.grid(), p.T)))
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (manufactured solution u=(t^2+1)x^2(1-x)^2, analytic source)",
+        "config": {**describe(p), "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (history ring %.0f MB)" % (M * n * 8 / 1e6)},
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "level_kernel", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                                    "(recipe nominal FP64 1.25 TFLOP/s)"},
+        "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max())},
+        "max_level_residual": float(res.max()),
+        "l2_error_vs_exact_at_T": err,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, d, cores, _ = oracle_sample(p, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                                "sample": d}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="large")
+    ap.add_argument("--precond", default=None, choices=[None, "strang", "tchan", "none"])
+    ap.add_argument("--levels", type=int, default=None, help="override M (exploration only)")
+    ap.add_argument("--maxit", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    p = workload(args.workload, args.precond)
+    if args.levels:
+        p.M = args.levels
+    if args.impl == "reference":
+        run_reference(args, p)
+    else:
+        run_native(args, p)
+
+
+if __name__ == "__main__":
+    main()

@@ -71,7 +71,9 @@ typedef struct tsfcde_options {
   const double *source_x;
   const double *source_t;
   int32_t levels_per_launch; /* device launches cover at most this many levels; 0 = no limit */
-  int32_t reserved[7];
+  void *stream;              /* cudaStream_t to run on (e.g. a PyTorch stream); NULL = the
+                                library creates and owns a non-blocking stream               */
+  int32_t reserved[6];
 } tsfcde_options;
 
 /* Fill `opt` with the defaults above (the paper's settings: Strang, tol 1e-12, x0 = 0). */
@@ -87,6 +89,7 @@ typedef struct tsfcde_stats {
   double max_residual;      /* largest final ||r||/||r_0|| among them                       */
   int32_t status;           /* worst device status seen (a TSFCDE_* code)                   */
   int32_t device_launches;  /* kernel launches the call made                                */
+  double device_ms;         /* device time of those launches (CUDA events on their stream)  */
 } tsfcde_stats;
 
 /* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */
@@ -129,7 +132,8 @@ int tsfcde_solve(tsfcde_ctx *ctx, double *u_out, tsfcde_stats *stats);
 /* Copy the current level u^j to the host buffer u_out (N values); *level receives j. */
 int tsfcde_get_level(tsfcde_ctx *ctx, double *u_out, int64_t *level);
 
-/* Return to level 0.  u0: N host values to use as u^0, or NULL to keep phi(x_i). */
+/* Return to level 0.  u0: N host values to use as u^0 (copied host to device), or NULL for
+ * phi(x_i) (restored from a device copy made at setup; no host transfer). */
 int tsfcde_reset(tsfcde_ctx *ctx, const double *u0);
 
 /* Per-level CGS iteration counts and final relative residuals of the levels advanced so far:

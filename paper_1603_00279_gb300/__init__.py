@@ -37,14 +37,16 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("preconditioner", C.c_int32), ("tol", C.c_double),
                 ("maxit", C.c_int32), ("device", C.c_int32), ("source_rank", C.c_int32),
                 ("source_x", C.POINTER(C.c_double)), ("source_t", C.POINTER(C.c_double)),
-                ("levels_per_launch", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Stats(C.Structure):
     _fields_ = [("level", C.c_int64), ("levels_advanced", C.c_int64),
                 ("total_iterations", C.c_int64), ("max_iterations", C.c_int32),
                 ("min_iterations", C.c_int32), ("max_residual", C.c_double),
-                ("status", C.c_int32), ("device_launches", C.c_int32)]
+                ("status", C.c_int32), ("device_launches", C.c_int32),
+                ("device_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,7 +121,8 @@ class Solver:
     def __init__(self, a, b, T, N, M, alpha, beta, gamma: Callable, d_plus: Callable,
                  d_minus: Callable, phi: Callable, f: Optional[Callable] = None,
                  separable=None, preconditioner: str = "strang", tol: float = 1e-12,
-                 maxit: int = 2000, device: int = 0, levels_per_launch: int = 0):
+                 maxit: int = 2000, device: int = 0, levels_per_launch: int = 0,
+                 stream: Optional[int] = None):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
         self.h = (b - a) / (N + 1)
@@ -148,6 +151,7 @@ class Solver:
         opt.maxit = maxit
         opt.device = device
         opt.levels_per_launch = levels_per_launch
+        opt.stream = stream
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
@@ -185,12 +189,17 @@ class Solver:
         _check(self.lib.tsfcde_step(self.ctx, nsteps, C.byref(s)), "tsfcde_step", True)
         return s.as_dict()
 
-    def solve(self, out: Optional[np.ndarray] = None):
-        out = np.empty(self.N) if out is None else out
+    def solve(self, out: Optional[np.ndarray] = None, out_ptr: Optional[int] = None):
+        """Advance to level M; copy u^M to `out` (numpy) or to the raw host address out_ptr."""
         s = Stats()
-        _check(self.lib.tsfcde_solve(self.ctx, _dptr(out), C.byref(s)), "tsfcde_solve", True)
+        if out_ptr is not None:
+            p = C.cast(C.c_void_p(out_ptr), C.POINTER(C.c_double))
+        else:
+            out = np.empty(self.N) if out is None else out
+            p = _dptr(out)
+        _check(self.lib.tsfcde_solve(self.ctx, p, C.byref(s)), "tsfcde_solve", True)
         self.last_stats = s.as_dict()
-        return out
+        return out if out_ptr is None else None
 
     def get_level(self):
         out = np.empty(self.N)
@@ -198,8 +207,12 @@ class Solver:
         _check(self.lib.tsfcde_get_level(self.ctx, _dptr(out), C.byref(j)), "tsfcde_get_level")
         return out, j.value
 
-    def reset(self, u0: Optional[np.ndarray] = None):
-        p = None if u0 is None else _dptr(np.ascontiguousarray(u0, dtype=np.float64))
+    def reset(self, u0: Optional[np.ndarray] = None, u0_ptr: Optional[int] = None):
+        """Back to level 0 with u^0 = u0 (numpy), the host address u0_ptr, or phi."""
+        if u0_ptr is not None:
+            p = C.cast(C.c_void_p(u0_ptr), C.POINTER(C.c_double))
+        else:
+            p = None if u0 is None else _dptr(np.ascontiguousarray(u0, dtype=np.float64))
         _check(self.lib.tsfcde_reset(self.ctx, p), "tsfcde_reset")
 
     def history(self, count: int):

@@ -30,8 +30,11 @@ struct tsfcde_ctx {
   double *ring = nullptr;
   std::vector<double> u0;
   double *omega = nullptr, *gtmp = nullptr;
+  double *u0dev = nullptr;   // device copy of phi(x_i), for tsfcde_reset(ctx, NULL)
   double2 *BhF = nullptr;
   double *gam = nullptr, *dp = nullptr, *dm = nullptr;
+  bool own_stream = true;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
@@ -128,7 +131,9 @@ void tsfcde_free(tsfcde_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->ring) cudaFree(c->ring);
   if (c->arena) cudaFree(c->arena);
-  if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -271,6 +276,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     A.resid = cv.take<double>(M);
     c->omega = cv.take<double>(n + 2);
     c->gtmp = cv.take<double>(n + 2);
+    c->u0dev = cv.take<double>(n);
     A.f_dense = f ? cv.take<double>((size_t)M * n) : nullptr;
     A.src_x = R > 0 ? cv.take<double>((size_t)R * n) : nullptr;
     A.src_t = R > 0 ? cv.take<double>((size_t)R * M) : nullptr;
@@ -301,6 +307,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
                        cudaMemcpyHostToDevice, c->stream));
   }
   CK(cudaMemcpyAsync(A.u, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->u0dev, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 
   // ---- device setup: weights (Lemma 2), time tables (Lemma 1), spectra ----
   int st = tsf::launch_weights(c->omega, c->gtmp, (int)n, c->beta, c->stream);
@@ -355,8 +362,19 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
   c->h = (b - a) / (double)(N + 1);
   c->tau = T / (double)M;
   c->sigma = 1.0 - alpha / 2.0;
-  if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaSetDevice(c->device) != cudaSuccess) {
     delete c;
+    return TSFCDE_E_CUDA;
+  }
+  if (o.stream) {
+    c->stream = (cudaStream_t)o.stream;
+    c->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return TSFCDE_E_CUDA;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    tsfcde_free(c);
     return TSFCDE_E_CUDA;
   }
   const int st = setup_impl(c, gamma, d_plus, d_minus, phi, f, user);
@@ -375,14 +393,20 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
   const int64_t j0 = c->level, j1 = c->level + nsteps;
   const int64_t chunk = c->opt.levels_per_launch > 0 ? c->opt.levels_per_launch : nsteps;
   int launches = 0, worst = TSFCDE_OK;
+  double dev_ms = 0.0;
   for (int64_t s = j0; s < j1; s += chunk) {
     const int64_t e = std::min(j1, s + chunk);
     int st = reset_device_flags(c);
     if (st) return st;
+    CK(cudaEventRecord(c->ev0, c->stream));
     st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
     if (st) return st;
+    CK(cudaEventRecord(c->ev1, c->stream));
     ++launches;
     CK(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    dev_ms += ms;
     int dst = 0;
     st = device_status(c, &dst);
     if (st) return st;
@@ -396,6 +420,7 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     stats->levels_advanced = nsteps;
     stats->status = worst;
     stats->device_launches = launches;
+    stats->device_ms = dev_ms;
     if (nsteps > 0) {
       std::vector<int> it(nsteps);
       std::vector<double> rs(nsteps);
@@ -435,9 +460,12 @@ int tsfcde_solve(tsfcde_ctx *c, double *u_out, tsfcde_stats *stats) {
 int tsfcde_reset(tsfcde_ctx *c, const double *u0) {
   if (!c) return TSFCDE_E_INVALID_ARG;
   CK(cudaSetDevice(c->device));
-  const double *src = u0 ? u0 : c->u0.data();
-  if (u0 && !all_finite(u0, c->n)) return TSFCDE_E_NONFINITE;
-  CK(cudaMemcpyAsync(c->A.u, src, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (u0) {
+    if (!all_finite(u0, c->n)) return TSFCDE_E_NONFINITE;
+    CK(cudaMemcpyAsync(c->A.u, u0, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(c->A.u, c->u0dev, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   c->level = 0;
   return TSFCDE_OK;
