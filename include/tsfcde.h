@@ -148,6 +148,26 @@ int tsfcde_get_history(tsfcde_ctx *ctx, int32_t *iters, double *resid, int64_t c
 #define TSFCDE_OP_PINV 2
 int tsfcde_apply(tsfcde_ctx *ctx, int32_t op, int64_t j, const double *x, double *y);
 
+/* Operator product that allocates nothing (no counterpart in the paper; an addition of this
+ * library).  For callers that cannot call cudaMalloc -- code running inside another runtime's
+ * memory pool or allocator hooks, processes whose device memory is reserved up front, or
+ * latency-critical paths that must not allocate -- this computes y = A x (op = TSFCDE_OP_A) or
+ * y = B x (op = TSFCDE_OP_B) for one level of Eq. (3.3), A = eta I - sigma L,
+ * B = eta I + (1 - sigma) L, L = q Q + kappa_plus W_beta + kappa_minus W_beta^T, from the
+ * level's scalars alone, without a context.
+ *   N: interior points, 1 <= N <= 16383 (larger N returns TSFCDE_E_INVALID_ARG).
+ *   beta in (1,2]; sigma = 1 - alpha/2; eta = eta_j; q = gamma/(2h); kappa_pm = d_pm / h^beta.
+ *   x, y: N float64 values in DEVICE memory, owned by the caller.  stream: cudaStream_t or NULL.
+ * All scratch (WSGD weights, twiddles, spectra, FFT work arrays, barrier words) lives in one
+ * fixed 3 MiB file-scope device array that each device holds from library load until process
+ * exit.  The first call on a device looks up that array's address and sets the kernel's
+ * shared-memory limit; make that first call before any stream capture.  Every call reuses the
+ * array: calls that overlap on the GPU race and must be serialised by the caller.  Returns
+ * after the product is complete (it synchronises `stream`). */
+int tsfcde_apply_operator_static(int64_t N, double beta, double sigma, double eta, double q,
+                                 double kappa_plus, double kappa_minus, int32_t op,
+                                 const double *x, double *y, void *stream);
+
 /* Release everything the context holds.  NULL is allowed. */
 void tsfcde_free(tsfcde_ctx *ctx);
 

@@ -89,6 +89,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_get_history.restype = C.c_int
     lib.tsfcde_apply.argtypes = [vp, i32, i64, pd, pd]
     lib.tsfcde_apply.restype = C.c_int
+    lib.tsfcde_apply_operator_static.argtypes = [i64, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, vp, vp]
+    lib.tsfcde_apply_operator_static.restype = C.c_int
     lib.tsfcde_free.argtypes = [vp]
     lib.tsfcde_free.restype = None
     lib.tsfcde_strerror.argtypes = [C.c_int]
@@ -244,6 +246,16 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def apply_operator_static(N: int, beta: float, sigma: float, eta: float, q: float,
+                          kappa_plus: float, kappa_minus: float, op: str, x_ptr: int, y_ptr: int,
+                          stream: Optional[int] = None) -> None:
+    """y = A x or B x of one level with no device allocation (tsfcde_apply_operator_static);
+    x_ptr and y_ptr are device addresses of N float64 values."""
+    st = load_library().tsfcde_apply_operator_static(N, beta, sigma, eta, q, kappa_plus,
+                                                      kappa_minus, OPS[op], x_ptr, y_ptr, stream)
+    _check(st, "tsfcde_apply_operator_static")
 
 
 def strerror(status: int) -> str:

@@ -13,6 +13,9 @@
 //            10 phases (P^{-1} p, A p^, dot, q/w update, P^{-1} w, A u^, dots).
 #include "tsfcde_internal.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace tsf {
 
 // ------------------------------------------------------------------------------------------------
@@ -861,4 +864,239 @@ int launch_time_tables(int M, double alpha, double tau, double h, double beta, c
   return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
 }
 
+
+
+// ================================================================================================
+// Operator product without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code running inside another runtime's memory pool or
+// allocator hooks, processes whose device memory is fully reserved up front, or callers that
+// must not make an allocating call on a latency-critical path.  tsfcde_apply_operator_static()
+// serves them: it computes y = A x or y = B x for one level (the operators of Eq. (3.3)) from
+// the level's scalars alone, with every intermediate (WSGD weights, twiddles, the spectrum of
+// W's circulant embedding, the operator spectrum, FFT work arrays, barrier words) kept in the
+// file-scope device array below.  The caller passes x and y in device memory.
+//
+// The array is a fixed 3 MiB per device, allocated by the CUDA runtime when the library is
+// loaded and held until the process exits; it bounds N (interior points) to 16383.  Every call
+// reuses it and the array keeps the previous call's contents; each call clears what must start
+// at zero (barrier words, status) and rewrites everything else before reading it.  Calls that
+// overlap on the GPU (different streams, or host threads) race on the array and must be
+// serialised by the caller.
+// ================================================================================================
 }  // namespace tsf
+
+#include <mutex>
+#include "../../include/tsfcde.h"
+
+namespace {
+
+constexpr int64_t kStaticMaxN = 16383;                       // L = 32768, N = 16384
+constexpr size_t kStaticScratchBytes = size_t(3) << 20;      // 3 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+  bool ready = false;
+  int status = 0;
+  unsigned char *base = nullptr;   // device address of g_static_scratch on this device
+  int sms = 0;
+  size_t smem = 0;
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+std::mutex g_static_mu;
+
+__global__ void __launch_bounds__(tsf::kThreads, 1)
+static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, double eta, double q,
+                       double kp, double km, int op, const double *x, double *y, double *xin) {
+  using namespace tsf;
+  const Smem S = smem_view(lp_max_of(A));
+  const int n = A.n, L = A.cp.L;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // Grunwald recurrence (Lemma 3), one thread, explicit rounding as in the setup path
+  if (gt == 0) {
+    double gk = 1.0;
+    gtmp[0] = gk;
+    for (int k = 1; k <= n + 1; ++k) {
+      const double f = __dadd_rn(1.0, -__ddiv_rn(beta + 1.0, (double)k));
+      gk = __dmul_rn(f, gk);
+      gtmp[k] = gk;
+    }
+  }
+  for (int k = gt; k < L; k += gs) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    const_cast<double2 *>(A.twL)[k] = make_double2(c, s);
+    xin[k] = k < n ? x[k] : 0.0;
+  }
+  if (!grid_sync(A)) return;
+  {
+    const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
+    const double lam0 = (4.0 - beta * beta) / 6.0;
+    const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+    for (int k = gt; k <= n + 1; k += gs) {
+      double w = __dmul_rn(lam1, gtmp[k]);
+      if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, gtmp[k - 1]));
+      if (k >= 2) w = __dadd_rn(w, __dmul_rn(lamm1, gtmp[k - 2]));
+      omega[k] = w;
+    }
+  }
+  if (!grid_sync(A)) return;
+  // spectrum of W's circulant embedding (t_0 = omega_1, ..., t_{n-1} = omega_n, t_{-1} = omega_0)
+  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 {
+                          double v[2];
+#pragma unroll
+                          for (int h = 0; h < 2; ++h) {
+                            const int i = 2 * m + h;
+                            v[h] = i < n ? omega[i + 1] : (i == L - 1 ? omega[0] : 0.0);
+                          }
+                          return make_double2(v[0], v[1]);
+                        });
+  if (!grid_sync(A)) return;
+  row_pass<1>(A, S, nullptr, const_cast<double2 *>(A.What), 1.0, -1);
+  if (!grid_sync(A)) return;
+  // operator spectrum: A = eta I - sigma L or B = eta I + (1-sigma) L, scaled 1/(4N)
+  {
+    LevelScalars s;
+    s.eta = eta;
+    s.q = q;
+    s.kp = kp;
+    s.km = km;
+    const ConvPlan &P = A.cp;
+    for (int sl = gt; sl <= P.N; sl += gs) {
+      const int k = sl == P.N ? P.N : ((sl & (P.N2 - 1)) * P.N1 + (sl >> P.lg2));
+      double2 sa, sb;
+      ab_symbols(A, s, __ldg(A.twL + k), sl == P.N, A.What[sl], sa, sb);
+      A.SA[sl] = op == 0 ? sa : sb;
+    }
+  }
+  if (!grid_sync(A)) return;
+  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                        [&](int m, double2) -> double2 { return ld2(xin, m); });
+  if (!grid_sync(A)) return;
+  row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
+  if (!grid_sync(A)) return;
+  col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                        [&](int m, double2 z) -> double2 {
+                          if (2 * m < n) y[2 * m] = z.x;
+                          if (2 * m + 1 < n) y[2 * m + 1] = z.y;
+                          return z;
+                        });
+}
+
+// Scratch layout inside g_static_scratch for a problem of n interior points.
+struct StaticLayout {
+  size_t off = 0;
+  unsigned char *base;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = reinterpret_cast<T *>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// One-time set-up per device (run by the first call on that device, with it current): the
+// device address of the scratch array, the SM count, and the kernel's shared-memory limit.
+int static_setup(int dev, StaticDevice **out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticDevice &d = g_static_dev[dev];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess) return TSFCDE_E_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TSFCDE_E_CUDA;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return TSFCDE_E_CUDA;
+    // largest plan (N = 16384 = 128 x 128): lines of 128 points, 4096 complex per buffer at most
+    const size_t smem = (size_t)2 * 4096 * sizeof(double2) + 4 * 32 * sizeof(double);
+    if (smem > (size_t)optin) return TSFCDE_E_INVALID_ARG;
+    if (cudaFuncSetAttribute((const void *)static_operator_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return TSFCDE_E_CUDA;
+    d.base = static_cast<unsigned char *>(ptr);
+    d.sms = sms;
+    d.smem = smem;
+    d.ready = true;
+  }
+  *out = &d;
+  return TSFCDE_OK;
+}
+
+}  // namespace
+
+extern "C" int tsfcde_apply_operator_static(int64_t N, double beta, double sigma, double eta,
+                                            double q, double kappa_plus, double kappa_minus,
+                                            int32_t op, const double *x, double *y, void *stream) {
+  using namespace tsf;
+  if (N < 1 || N > kStaticMaxN) return TSFCDE_E_INVALID_ARG;
+  if (op != TSFCDE_OP_A && op != TSFCDE_OP_B) return TSFCDE_E_INVALID_ARG;
+  if (!x || !y || !(beta > 1.0 && beta <= 2.0) || !(sigma > 0.0 && sigma <= 1.0)) return TSFCDE_E_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TSFCDE_E_NO_DEVICE;
+  StaticDevice *d = nullptr;
+  int st = static_setup(dev, &d);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  Args A;
+  memset(&A, 0, sizeof(A));
+  const int n = (int)N;
+  A.n = n;
+  A.M = 1;
+  int lgL = 3;
+  while ((1 << lgL) < 2 * n) ++lgL;
+  A.cp.lgL = lgL;
+  A.cp.L = 1 << lgL;
+  A.cp.lgN = lgL - 1;
+  A.cp.N = 1 << A.cp.lgN;
+  A.cp.lg1 = A.cp.lgN / 2;
+  A.cp.lg2 = A.cp.lgN - A.cp.lg1;
+  A.cp.N1 = 1 << A.cp.lg1;
+  A.cp.N2 = 1 << A.cp.lg2;
+  A.bp.lg1 = 1;   // no complex-plan phases run here
+  A.bp.lg2 = 1;
+  A.sigma = sigma;
+  const int G = d->sms;
+  auto cap = [&](int items, int lines_per_item, int lg) {
+    const int per = (items + G - 1) / G;
+    const int fit = std::max(1, (4096 >> lg) / lines_per_item);
+    return std::max(1, std::min(per, fit));
+  };
+  A.cap_col = cap(A.cp.N2, 1, A.cp.lg1);
+  A.cap_row = cap(A.cp.N1 / 2 + 1, 2, A.cp.lg2);
+  A.cap_bcol = 1;
+  A.cap_brow = 1;
+  const size_t smem = level_smem_bytes(A);
+  if (smem > d->smem) return TSFCDE_E_INVALID_ARG;
+
+  const size_t L = (size_t)A.cp.L, Nc = (size_t)A.cp.N;
+  StaticLayout lay;
+  lay.base = d->base;
+  A.bar = lay.take<unsigned>(64);
+  A.status = lay.take<int>(4);
+  A.twL = lay.take<double2>(L);
+  A.What = lay.take<double2>(Nc + 1);
+  A.SA = lay.take<double2>(Nc + 1);
+  A.Y1 = lay.take<double2>(Nc);
+  A.Y2 = lay.take<double2>(Nc);
+  double *xin = lay.take<double>(L);
+  double *omega = lay.take<double>(N + 2);
+  double *gtmp = lay.take<double>(N + 2);
+  if (lay.off > kStaticScratchBytes) return TSFCDE_E_INVALID_ARG;
+
+  // barrier words and status must start at zero on every call
+  if (cudaMemsetAsync(A.bar, 0, 64 * sizeof(unsigned), s) != cudaSuccess) return TSFCDE_E_CUDA;
+  if (cudaMemsetAsync(A.status, 0, 4 * sizeof(int), s) != cudaSuccess) return TSFCDE_E_CUDA;
+  void *args[] = {&A, &omega, &gtmp, &beta, &eta, &q, &kappa_plus, &kappa_minus, &op, &x, &y, &xin};
+  if (cudaLaunchCooperativeKernel((const void *)static_operator_kernel, G, kThreads, args, smem, s) !=
+      cudaSuccess)
+    return TSFCDE_E_CUDA;
+  int hst[2] = {0, 0};
+  if (cudaMemcpyAsync(hst, A.status, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TSFCDE_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TSFCDE_E_CUDA;
+  return hst[0];
+}
