@@ -280,7 +280,8 @@ def run_native(args, p):
                      "traffic": None,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                     "(recipe nominal FP64 1.25 TFLOP/s)"},
-        "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max())},
+        "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max()),
+                           "levels_at_maxit": int((it >= args.maxit).sum())},
         "max_level_residual": float(res.max()),
         "l2_error_vs_exact_at_T": err,
         "clocks": clocks,

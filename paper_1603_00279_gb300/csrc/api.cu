@@ -85,7 +85,7 @@ int device_status(tsfcde_ctx *c, int *st) {
 }
 
 int reset_device_flags(tsfcde_ctx *c) {
-  CK(cudaMemsetAsync(c->A.bar, 0, 64 * sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->A.bar, 0, tsf::kBarWords * sizeof(unsigned), c->stream));
   CK(cudaMemsetAsync(c->A.status, 0, 4 * sizeof(int), c->stream));
   return TSFCDE_OK;
 }
@@ -202,7 +202,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, c->device));
-  c->grid = prop.multiProcessorCount;
+  c->grid = std::min(prop.multiProcessorCount, tsf::kMaxGrid);
   const int G = c->grid;
   const int budget = 4096;   // complex values per ping-pong buffer
   auto cap = [&](int items, int lines_per_item, int lg) {
@@ -270,7 +270,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     c->dp = cv.take<double>(M);
     c->dm = cv.take<double>(M);
     A.partials = cv.take<double>((size_t)2 * G * 4);
-    A.bar = cv.take<unsigned>(64);
+    A.bar = cv.take<unsigned>(tsf::kBarWords);
     A.status = cv.take<int>(4);
     A.iters = cv.take<int>(M);
     A.resid = cv.take<double>(M);

@@ -23,15 +23,21 @@ namespace tsf {
 // ------------------------------------------------------------------------------------------------
 struct Smem {
   double2 *a, *b;   // ping-pong line buffers
+  double2 *tw;      // twiddles of the current pass's line length, e^{-2 pi i m / P}
   double *red;      // reduction scratch (4 * 32 doubles)
 };
 
-__device__ __forceinline__ Smem smem_view(int lp_max) {
+__device__ __forceinline__ int tw_max_of(const Args &A) {
+  return 1 << max(max(A.cp.lg1, A.cp.lg2), max(A.bp.lg1, A.bp.lg2));
+}
+
+__device__ __forceinline__ Smem smem_view(int lp_max, int tw_max) {
   extern __shared__ double2 dsm[];
   Smem s;
   s.a = dsm;
   s.b = dsm + lp_max;
-  s.red = reinterpret_cast<double *>(dsm + 2 * lp_max);
+  s.tw = dsm + 2 * lp_max;
+  s.red = reinterpret_cast<double *>(dsm + 2 * lp_max + tw_max);
   return s;
 }
 
@@ -41,6 +47,14 @@ __device__ __forceinline__ int lp_max_of(const Args &A) {
   m = max(m, A.cap_bcol << A.bp.lg1);
   m = max(m, A.cap_brow << A.bp.lg2);
   return m;
+}
+
+// Fill S.tw with the line twiddles e^{-2 pi i m / 2^lgP}, m < 2^lgP (a subset of the L table).
+__device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S, int lgP) {
+  __syncthreads();
+  const int P = 1 << lgP, sh = A.cp.lgL - lgP;
+  for (int m = threadIdx.x; m < P; m += blockDim.x) S.tw[m] = __ldg(A.twL + (m << sh));
+  __syncthreads();
 }
 
 // Contiguous item range of this CTA: [lo, hi).
@@ -59,13 +73,13 @@ __device__ __forceinline__ void my_items(int nitems, int &lo, int &hi) {
 // ------------------------------------------------------------------------------------------------
 template <bool INV, bool FWD, class Body>
 __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, int lg2, int tws,
-                                         int cap, const double2 *__restrict__ Yin,
-                                         double2 *__restrict__ Yout, Body body) {
+                                         int cap, const double2 *Yin, double2 *Yout,
+                                         Body body) {
   const int P1 = 1 << lg1, P2 = 1 << lg2;
   const double2 *__restrict__ tw = A.twL;
-  const int lgT = A.cp.lgL;
   int lo, hi;
   my_items(P2, lo, hi);
+  if (lo < hi) load_line_twiddles(A, S, lg1);
   for (int c0 = lo; c0 < hi; c0 += cap) {
     const int cnt = min(cap, hi - c0);
     double2 *a = S.a, *b = S.b;
@@ -75,7 +89,7 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, 
         a[(l << lg1) + k1] = cmulc(Yin[(k1 << lg2) + m2], __ldg(tw + ((m2 * k1) << tws)));
       }
       __syncthreads();
-      a = smem_fft<+1>(a, b, lg1, cnt, tw, lgT);
+      a = smem_fft<+1>(a, b, lg1, cnt, S.tw, lg1);
       b = (a == S.a) ? S.b : S.a;
     }
     for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
@@ -85,7 +99,7 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, 
     }
     __syncthreads();
     if (FWD) {
-      a = smem_fft<-1>(a, b, lg1, cnt, tw, lgT);
+      a = smem_fft<-1>(a, b, lg1, cnt, S.tw, lg1);
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
         Yout[(k1 << lg2) + m2] = cmul(a[(l << lg1) + k1], __ldg(tw + ((m2 * k1) << tws)));
@@ -132,14 +146,15 @@ __device__ __forceinline__ void ab_symbols(const Args &A, const LevelScalars &s,
 }
 
 template <int MODE>
-__device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const double2 *__restrict__ Sym,
-                                         double2 *__restrict__ Sout, double scale, int sym_level) {
+__device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const double2 *Sym,
+                                         double2 *Sout, double scale, int sym_level) {
   const ConvPlan &P = A.cp;
   const int N1 = P.N1, N2 = P.N2, lg2 = P.lg2, N = P.N;
   const double2 *__restrict__ tw = A.twL;
   const int nitems = N1 / 2 + 1;
   int lo, hi;
   my_items(nitems, lo, hi);
+  if (lo < hi) load_line_twiddles(A, S, lg2);
   LevelScalars ls;
   if (MODE == 1 && sym_level >= 0) ls = level_scalars(A, sym_level);
   for (int i0 = lo; i0 < hi; i0 += A.cap_row) {
@@ -154,7 +169,7 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const dou
       a[e] = A.Y1[(row << lg2) + k2];
     }
     __syncthreads();
-    a = smem_fft<-1>(a, b, lg2, nl, tw, P.lgL);
+    a = smem_fft<-1>(a, b, lg2, nl, S.tw, lg2);
     b = (a == S.a) ? S.b : S.a;
     // split / multiply / merge, pairwise in k and N-k
     for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
@@ -218,7 +233,7 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const dou
     }
     __syncthreads();
     if (MODE == 0) {
-      a = smem_fft<+1>(a, b, lg2, nl, tw, P.lgL);
+      a = smem_fft<+1>(a, b, lg2, nl, S.tw, lg2);
       for (int e = threadIdx.x; e < nl * N2; e += blockDim.x) {
         const int line = e >> lg2, k2 = e & (N2 - 1);
         const int it = i0 + (line >> 1);
@@ -236,23 +251,24 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const dou
 // Tab (permuted) and inverse row FFT into Y2 (MODE 0) or store the spectrum * scale (MODE 1).
 // ------------------------------------------------------------------------------------------------
 template <int MODE>
-__device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const double2 *__restrict__ Tab,
-                                          double2 *__restrict__ Out, double scale) {
+__device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const double2 *Tab,
+                                          double2 *Out, double scale) {
   const CplxPlan &P = A.bp;
   const int lg2 = P.lg2, N2 = P.N2;
   int lo, hi;
   my_items(P.N1, lo, hi);
+  if (lo < hi) load_line_twiddles(A, S, lg2);
   for (int r0 = lo; r0 < hi; r0 += A.cap_brow) {
     const int cnt = min(A.cap_brow, hi - r0);
     double2 *a = S.a, *b = S.b;
     for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = A.Y1[(r0 << lg2) + e];
     __syncthreads();
-    a = smem_fft<-1>(a, b, lg2, cnt, A.twL, A.cp.lgL);
+    a = smem_fft<-1>(a, b, lg2, cnt, S.tw, lg2);
     b = (a == S.a) ? S.b : S.a;
     if (MODE == 0) {
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = cmul(a[e], Tab[(r0 << lg2) + e]);
       __syncthreads();
-      a = smem_fft<+1>(a, b, lg2, cnt, A.twL, A.cp.lgL);
+      a = smem_fft<+1>(a, b, lg2, cnt, S.tw, lg2);
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) A.Y2[(r0 << lg2) + e] = a[e];
     } else {
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) Out[(r0 << lg2) + e] = cscale(a[e], scale);
@@ -444,7 +460,8 @@ __device__ bool level_symbols(const Args &A, const Smem &S, int j) {
 // the level kernel
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int j1) {
-  const Smem S = smem_view(lp_max_of(A));
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
   const int n = A.n;
   const bool pc = A.precond != 2;
   int rb = 0;
@@ -621,7 +638,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
 // diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}); x and y are padded device vectors.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int j, const double *xin, double *yout) {
-  const Smem S = smem_view(lp_max_of(A));
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
   const int n = A.n;
   if (!level_symbols(A, S, j)) return;
   col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
@@ -660,7 +678,8 @@ __device__ __forceinline__ double circ_col(const double *omega, int which, int k
 }
 
 __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T) {
-  const Smem S = smem_view(lp_max_of(A));
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
   const int n = A.n, L = A.cp.L;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   // tables: twiddles e^{-2 pi i k/L}, chirp e^{i pi (k^2 mod 2n)/n}
@@ -806,7 +825,10 @@ size_t level_smem_bytes(const Args &A) {
   m = m > ((2 * A.cap_row) << A.cp.lg2) ? m : ((2 * A.cap_row) << A.cp.lg2);
   m = m > (A.cap_bcol << A.bp.lg1) ? m : (A.cap_bcol << A.bp.lg1);
   m = m > (A.cap_brow << A.bp.lg2) ? m : (A.cap_brow << A.bp.lg2);
-  return (size_t)2 * m * sizeof(double2) + 4 * 32 * sizeof(double);
+  int lt = A.cp.lg1 > A.cp.lg2 ? A.cp.lg1 : A.cp.lg2;
+  lt = lt > A.bp.lg1 ? lt : A.bp.lg1;
+  lt = lt > A.bp.lg2 ? lt : A.bp.lg2;
+  return (size_t)(2 * m + (1 << lt)) * sizeof(double2) + 4 * 32 * sizeof(double);
 }
 
 const void *level_kernel_ptr() { return (const void *)level_kernel; }
@@ -910,7 +932,8 @@ __global__ void __launch_bounds__(tsf::kThreads, 1)
 static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, double eta, double q,
                        double kp, double km, int op, const double *x, double *y, double *xin) {
   using namespace tsf;
-  const Smem S = smem_view(lp_max_of(A));
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
   const int n = A.n, L = A.cp.L;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   // Grunwald recurrence (Lemma 3), one thread, explicit rounding as in the setup path
@@ -1012,7 +1035,7 @@ int static_setup(int dev, StaticDevice **out) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return TSFCDE_E_CUDA;
     // largest plan (N = 16384 = 128 x 128): lines of 128 points, 4096 complex per buffer at most
-    const size_t smem = (size_t)2 * 4096 * sizeof(double2) + 4 * 32 * sizeof(double);
+    const size_t smem = (size_t)(2 * 4096 + 4096) * sizeof(double2) + 4 * 32 * sizeof(double);
     if (smem > (size_t)optin) return TSFCDE_E_INVALID_ARG;
     if (cudaFuncSetAttribute((const void *)static_operator_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -1060,7 +1083,7 @@ extern "C" int tsfcde_apply_operator_static(int64_t N, double beta, double sigma
   A.bp.lg1 = 1;   // no complex-plan phases run here
   A.bp.lg2 = 1;
   A.sigma = sigma;
-  const int G = d->sms;
+  const int G = std::min(d->sms, kMaxGrid);
   auto cap = [&](int items, int lines_per_item, int lg) {
     const int per = (items + G - 1) / G;
     const int fit = std::max(1, (4096 >> lg) / lines_per_item);
@@ -1076,7 +1099,7 @@ extern "C" int tsfcde_apply_operator_static(int64_t N, double beta, double sigma
   const size_t L = (size_t)A.cp.L, Nc = (size_t)A.cp.N;
   StaticLayout lay;
   lay.base = d->base;
-  A.bar = lay.take<unsigned>(64);
+  A.bar = lay.take<unsigned>(kBarWords);
   A.status = lay.take<int>(4);
   A.twL = lay.take<double2>(L);
   A.What = lay.take<double2>(Nc + 1);
@@ -1089,7 +1112,7 @@ extern "C" int tsfcde_apply_operator_static(int64_t N, double beta, double sigma
   if (lay.off > kStaticScratchBytes) return TSFCDE_E_INVALID_ARG;
 
   // barrier words and status must start at zero on every call
-  if (cudaMemsetAsync(A.bar, 0, 64 * sizeof(unsigned), s) != cudaSuccess) return TSFCDE_E_CUDA;
+  if (cudaMemsetAsync(A.bar, 0, kBarWords * sizeof(unsigned), s) != cudaSuccess) return TSFCDE_E_CUDA;
   if (cudaMemsetAsync(A.status, 0, 4 * sizeof(int), s) != cudaSuccess) return TSFCDE_E_CUDA;
   void *args[] = {&A, &omega, &gtmp, &beta, &eta, &q, &kappa_plus, &kappa_minus, &op, &x, &y, &xin};
   if (cudaLaunchCooperativeKernel((const void *)static_operator_kernel, G, kThreads, args, smem, s) !=

@@ -67,7 +67,7 @@ struct Args {
   double2 *Y1, *Y2;       // FFT work, L complex each
   double *cprime;         // first column of P^{-1}, n
   double *partials;       // 2 x gridDim x 4
-  unsigned *bar;          // [0] arrival count, [32] generation
+  unsigned *bar;          // kBarWords barrier words: [0, 2) 64-bit arrival counter
   int *status;            // [0] status, [1] abort flag
   int *iters;             // M
   double *resid;          // M
@@ -92,7 +92,8 @@ __device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, 
 // ---------------------------------------------------------------------------------------------
 // Stockham radix-4/2 FFT of `nl` lines of length P = 2^lgP in shared memory.
 // Line l occupies a[l*P .. l*P+P); b is a scratch area of the same size.  SIGN = -1 forward,
-// +1 inverse (unnormalised).  Twiddles come from tw[k] = e^{-2 pi i k / 2^lgT}, 2^lgT >= P.
+// +1 inverse (unnormalised).  Twiddles come from tw[k] = e^{-2 pi i k / 2^lgT}, 2^lgT >= P
+// (a shared-memory table of the line length in every caller).
 // All threads of the CTA take part; returns the buffer holding the result.
 // Stage with current sub-length Ls and radix r: for j < P/r, k = j mod Ls, a_q = x[j + q P/r]
 // is twiddled by e^{SIGN 2 pi i q k/(r Ls)}, an r-point DFT is taken, and output q goes to
@@ -100,7 +101,7 @@ __device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, 
 // ---------------------------------------------------------------------------------------------
 template <int SIGN>
 __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, int nl,
-                                             const double2 *__restrict__ tw, int lgT) {
+                                             const double2 *tw, int lgT) {
   const int P = 1 << lgP;
   int lgLs = 0;
   while (lgLs < lgP) {
@@ -117,9 +118,9 @@ __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, in
         double2 *y = b + l * P;
         double2 a0 = x[j], a1 = x[j + Q], a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
         if (k) {
-          double2 w1 = __ldg(tw + ((k) << sh));
-          double2 w2 = __ldg(tw + ((2 * k) << sh));
-          double2 w3 = __ldg(tw + ((3 * k) << sh));
+          double2 w1 = tw[k << sh];
+          double2 w2 = tw[(2 * k) << sh];
+          double2 w3 = tw[(3 * k) << sh];
           if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
           a1 = cmul(a1, w1);
           a2 = cmul(a2, w2);
@@ -146,7 +147,7 @@ __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, in
         double2 *y = b + l * P;
         double2 a0 = x[j], a1 = x[j + Q];
         if (k) {
-          double2 w1 = __ldg(tw + (k << sh));
+          double2 w1 = tw[k << sh];
           if (SIGN > 0) w1 = cconj(w1);
           a1 = cmul(a1, w1);
         }
@@ -184,31 +185,52 @@ __device__ __forceinline__ void raise_fatal(const Args &A, int code) {
   __threadfence();
 }
 
-// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after kSpinLimit polls the
-// CTA records E_TIMEOUT, raises the abort flag and leaves.  Returns false when the kernel must
-// stop (abort raised anywhere); all CTAs then return without touching the barrier again.
+// Barrier words: [0, 2) the 64-bit arrival counter; the rest is reserved.
+constexpr int kMaxGrid = 1024;
+constexpr int kBarWords = 32 + kMaxGrid;
+
+// Per-CTA count of grid barriers passed in this launch.
+__device__ __forceinline__ unsigned long long &bar_count() {
+  __shared__ unsigned long long k;
+  return k;
+}
+// Run once at the start of every kernel that calls grid_sync.
+__device__ __forceinline__ void grid_sync_init() {
+  if (threadIdx.x == 0) bar_count() = 0ull;
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch: a 64-bit arrival counter that only grows during
+// a launch (zeroed by the host before it).  At its k-th barrier a CTA adds 1 with release
+// semantics and waits until the counter reaches k * gridDim.x.  Every wait is bounded: after
+// kSpinLimit polls the CTA records E_TIMEOUT, raises the abort flag and leaves.  Returns false
+// when the kernel must stop (abort raised anywhere); all CTAs then return without touching the
+// barrier again.
 __device__ __forceinline__ bool grid_sync(const Args &A) {
   __shared__ int s_go;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned *count = A.bar;
-    unsigned *gen = A.bar + 32;
-    const unsigned g = ld_acquire_u32(gen);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(A.bar);
+    const unsigned long long k = ++bar_count();
+    const unsigned long long target = k * (unsigned long long)gridDim.x;
     __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      st_release_u32(gen, g + 1);
-    } else {
-      long long spins = 0;
-      while (ld_acquire_u32(gen) == g) {
-        if (++spins > kSpinLimit) {
-          raise_fatal(A, kETimeout);
-          break;
-        }
-        if ((spins & 255) == 0 && ld_volatile_i32(A.status + 1)) break;
+    red_add_release_u64(cnt, 1ull);
+    long long spins = 0;
+    while (ld_acquire_u64(cnt) < target) {
+      if (++spins > kSpinLimit) {
+        raise_fatal(A, kETimeout);
+        break;
       }
+      if ((spins & 255) == 0 && ld_volatile_i32(A.status + 1)) break;
     }
     __threadfence();
     s_go = ld_volatile_i32(A.status + 1) == 0;

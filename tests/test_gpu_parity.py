@@ -110,7 +110,9 @@ def test_separable_source_equals_callback():
     u1, u2 = s1.solve(), s2.solve()
     s1.close()
     s2.close()
-    assert rel_l2(u1, u2) < 1e-12
+    # both marches stop at ||r||/||r0|| < 1e-12, so they agree to the parity tolerance, not to
+    # the last bit
+    assert rel_l2(u1, u2) < 1e-10
 
 
 def test_unpreconditioned_matches():
