@@ -201,7 +201,7 @@ def run_native(args, p):
 
     stream = torch.cuda.Stream()
     s = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
-                              maxit=args.maxit)
+                              maxit=args.maxit, precision=args.precision)
     n, M = p.n, p.M
 
     def one_step():
@@ -268,7 +268,8 @@ def run_native(args, p):
     line = {
         "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 inner / f64 refinement",
         "data": "synthetic (manufactured solution u=(t^2+1)x^2(1-x)^2, analytic source)",
         "config": {**describe(p), "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (history ring %.0f MB)" % (M * n * 8 / 1e6)},
@@ -283,6 +284,9 @@ def run_native(args, p):
         "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max()),
                            "levels_at_maxit": int((it >= args.maxit).sum())},
         "max_level_residual": float(res.max()),
+        "refinement": ({"outer_steps": int(sum(st["outer_iterations"] for st in stats)) // max(1, args.steps),
+                        "escalated_levels": int(sum(st["escalated_levels"] for st in stats)) // max(1, args.steps)}
+                       if args.precision == "mixed" else None),
         "l2_error_vs_exact_at_T": err,
         "clocks": clocks,
     }
@@ -303,12 +307,16 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="large")
     ap.add_argument("--precond", default=None, choices=[None, "strang", "tchan", "none"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"],
+                    help="default: fp64, or mixed for the mixed workload")
     ap.add_argument("--levels", type=int, default=None, help="override M (exploration only)")
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     p = workload(args.workload, args.precond)
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "mixed" else "fp64"
     if args.levels:
         p.M = args.levels
     if args.impl == "reference":

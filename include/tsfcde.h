@@ -54,10 +54,16 @@ extern "C" {
 #define TSFCDE_PRECOND_TCHAN 1  /* T. Chan's optimal circulant in place of s(.)                  */
 #define TSFCDE_PRECOND_NONE 2   /* plain CGS                                                     */
 
-#define TSFCDE_FP64 0 /* every step in float64 */
+#define TSFCDE_FP64 0  /* every step in float64                                             */
+#define TSFCDE_MIXED 1 /* iterative refinement: residual r = g - A x, solution update, history
+                          sum and all spectra/weights in float64; CGS on A d = r in float32
+                          (float32 FFTs, matvecs and preconditioner, spectra rounded from
+                          float64); a level whose float64 residual stops falling by half per
+                          refinement step, or whose float32 solve breaks down, is finished by
+                          the float64 CGS from the current iterate (counted as escalated)   */
 
 typedef struct tsfcde_options {
-  int32_t precision;      /* TSFCDE_FP64                                                   */
+  int32_t precision;      /* TSFCDE_FP64 (default) or TSFCDE_MIXED                         */
   int32_t preconditioner; /* TSFCDE_PRECOND_*; default STRANG                               */
   double tol;             /* CGS stop: ||r_k||_2 / ||r_0||_2 < tol (Section 4); default 1e-12 */
   int32_t maxit;          /* CGS iterations per level before E_NOT_CONVERGED; default 2000  */
@@ -73,7 +79,10 @@ typedef struct tsfcde_options {
   int32_t levels_per_launch; /* device launches cover at most this many levels; 0 = no limit */
   void *stream;              /* cudaStream_t to run on (e.g. a PyTorch stream); NULL = the
                                 library creates and owns a non-blocking stream               */
-  int32_t reserved[6];
+  double inner_tol;          /* MIXED: relative residual of each float32 solve; default 1e-5  */
+  int32_t inner_maxit;       /* MIXED: float32 CGS iterations per refinement step; default 200 */
+  int32_t outer_maxit;       /* MIXED: refinement steps per level before escalation; default 12 */
+  int32_t reserved[4];
 } tsfcde_options;
 
 /* Fill `opt` with the defaults above (the paper's settings: Strang, tol 1e-12, x0 = 0). */
@@ -90,6 +99,9 @@ typedef struct tsfcde_stats {
   int32_t status;           /* worst device status seen (a TSFCDE_* code)                   */
   int32_t device_launches;  /* kernel launches the call made                                */
   double device_ms;         /* device time of those launches (CUDA events on their stream)  */
+  int64_t outer_iterations; /* MIXED: refinement steps summed over the levels advanced      */
+  int32_t escalated_levels; /* MIXED: levels finished by the float64 CGS                    */
+  int32_t pad_;
 } tsfcde_stats;
 
 /* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */

@@ -26,6 +26,7 @@ STATUS_NAMES = {
     9: "E_STATE", 10: "E_NO_DEVICE",
 }
 PRECONDITIONERS = {"strang": 0, "tchan": 1, "none": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 OPS = {"A": 0, "B": 1, "Pinv": 2}
 
 COEF_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
@@ -38,7 +39,8 @@ class Options(C.Structure):
                 ("maxit", C.c_int32), ("device", C.c_int32), ("source_rank", C.c_int32),
                 ("source_x", C.POINTER(C.c_double)), ("source_t", C.POINTER(C.c_double)),
                 ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
-                ("reserved", C.c_int32 * 6)]
+                ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -46,7 +48,8 @@ class Stats(C.Structure):
                 ("total_iterations", C.c_int64), ("max_iterations", C.c_int32),
                 ("min_iterations", C.c_int32), ("max_residual", C.c_double),
                 ("status", C.c_int32), ("device_launches", C.c_int32),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("outer_iterations", C.c_int64),
+                ("escalated_levels", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,7 +127,9 @@ class Solver:
                  d_minus: Callable, phi: Callable, f: Optional[Callable] = None,
                  separable=None, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, device: int = 0, levels_per_launch: int = 0,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, precision: str = "fp64",
+                 inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
+                 outer_maxit: Optional[int] = None):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
         self.h = (b - a) / (N + 1)
@@ -154,6 +159,13 @@ class Solver:
         opt.device = device
         opt.levels_per_launch = levels_per_launch
         opt.stream = stream
+        opt.precision = PRECISIONS[precision]
+        if inner_tol is not None:
+            opt.inner_tol = inner_tol
+        if inner_maxit is not None:
+            opt.inner_maxit = inner_maxit
+        if outer_maxit is not None:
+            opt.outer_maxit = outer_maxit
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:

@@ -104,6 +104,10 @@ void tsfcde_default_options(tsfcde_options *opt) {
   opt->device = 0;
   opt->source_rank = 0;
   opt->levels_per_launch = 0;
+  opt->stream = nullptr;
+  opt->inner_tol = 1e-5;
+  opt->inner_maxit = 200;
+  opt->outer_maxit = 12;
 }
 
 const char *tsfcde_strerror(int status) {
@@ -198,6 +202,11 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   A.tol = c->opt.tol;
   A.maxit = c->opt.maxit;
   A.src_rank = R;
+  A.precision = c->opt.precision;
+  A.inner_tol = c->opt.inner_tol;
+  A.inner_maxit = c->opt.inner_maxit;
+  A.outer_maxit = c->opt.outer_maxit;
+  const bool mixed = A.precision == TSFCDE_MIXED;
 
   // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
   cudaDeviceProp prop;
@@ -277,6 +286,23 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     c->omega = cv.take<double>(n + 2);
     c->gtmp = cv.take<double>(n + 2);
     c->u0dev = cv.take<double>(n);
+    A.outer_iters = cv.take<int>(M);
+    A.escalated = cv.take<int>(M);
+    if (mixed) {
+      A.g = cv.take<double>(Lp);
+      A.x32 = cv.take<float>(Lp);
+      A.r32 = cv.take<float>(Lp);
+      A.rt32 = cv.take<float>(Lp);
+      A.p32 = cv.take<float>(Lp);
+      A.q32 = cv.take<float>(Lp);
+      A.uu32 = cv.take<float>(Lp);
+      A.vh32 = cv.take<float>(Lp);
+      A.SA32 = cv.take<float2>(N + 1);
+      A.SP32 = cv.take<float2>(N + 1);
+      A.Y1f = cv.take<float2>(N);
+      A.Y2f = cv.take<float2>(N);
+      A.twL32 = cv.take<float2>(Lp);
+    }
     A.f_dense = f ? cv.take<double>((size_t)M * n) : nullptr;
     A.src_x = R > 0 ? cv.take<double>((size_t)R * n) : nullptr;
     A.src_t = R > 0 ? cv.take<double>((size_t)R * M) : nullptr;
@@ -344,8 +370,11 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
   tsfcde_options o;
   tsfcde_default_options(&o);
   if (opt) o = *opt;
-  if (o.preconditioner < 0 || o.preconditioner > 2 || o.precision != TSFCDE_FP64 || !(o.tol > 0) ||
-      o.maxit < 1 || o.source_rank < 0 || (o.source_rank > 0 && (!o.source_x || !o.source_t || f)))
+  if (o.preconditioner < 0 || o.preconditioner > 2 ||
+      (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1 ||
+      o.source_rank < 0 || (o.source_rank > 0 && (!o.source_x || !o.source_t || f)))
+    return TSFCDE_E_INVALID_ARG;
+  if (o.precision == TSFCDE_MIXED && (!(o.inner_tol > 0 && o.inner_tol < 1) || o.inner_maxit < 1 || o.outer_maxit < 1))
     return TSFCDE_E_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
@@ -426,6 +455,15 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
       std::vector<double> rs(nsteps);
       CK(cudaMemcpy(it.data(), c->A.iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(rs.data(), c->A.resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+      if (c->A.precision == TSFCDE_MIXED) {
+        std::vector<int> oi(nsteps), es(nsteps);
+        CK(cudaMemcpy(oi.data(), c->A.outer_iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(es.data(), c->A.escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < nsteps; ++k) {
+          stats->outer_iterations += oi[k];
+          stats->escalated_levels += es[k];
+        }
+      }
       stats->min_iterations = it[0];
       for (int64_t k = 0; k < nsteps; ++k) {
         stats->total_iterations += it[k];

@@ -8,9 +8,12 @@
 //            forward FFT and the spectra of A, B, P^{-1} (2 phases)               [Eq. (3.7)]
 //   RHS      commit of the previous level + history sum of Lemma 1 + column FFT of u^j; row
 //            pass with B's spectrum; column pass giving g = B u^j - hscale*H + f  [Eq. (3.1)]
-//   CGS      preconditioned CGS from x0 = 0 (Section 4), the elementwise updates and dot
+//   solve    FP64: preconditioned CGS from x0 = 0 (Section 4), the elementwise updates and dot
 //            products fused into the column passes of the FFT convolutions; each iteration is
 //            10 phases (P^{-1} p, A p^, dot, q/w update, P^{-1} w, A u^, dots).
+//            Mixed: iterative refinement whose residual r = g - A x, solution update and history
+//            stay in FP64, with the same CGS run in FP32 (FP32 FFTs, spectra rounded from FP64)
+//            on A d = r; a level whose FP64 residual stops falling is finished by the FP64 CGS.
 #include "tsfcde_internal.cuh"
 
 #include <algorithm>
@@ -19,12 +22,12 @@
 namespace tsf {
 
 // ------------------------------------------------------------------------------------------------
-// per-CTA shared memory view
+// per-CTA shared memory view (sized for FP64 lines; FP32 passes use the same regions)
 // ------------------------------------------------------------------------------------------------
 struct Smem {
-  double2 *a, *b;   // ping-pong line buffers
-  double2 *tw;      // twiddles of the current pass's line length, e^{-2 pi i m / P}
-  double *red;      // reduction scratch (4 * 32 doubles)
+  void *a, *b;   // ping-pong line buffers
+  void *tw;      // twiddles of the current pass's line length, e^{-2 pi i m / P}
+  double *red;   // reduction scratch (4 * 32 doubles)
 };
 
 __device__ __forceinline__ int tw_max_of(const Args &A) {
@@ -50,10 +53,12 @@ __device__ __forceinline__ int lp_max_of(const Args &A) {
 }
 
 // Fill S.tw with the line twiddles e^{-2 pi i m / 2^lgP}, m < 2^lgP (a subset of the L table).
-__device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S, int lgP) {
+template <typename T>
+__device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S, const T *twG, int lgP) {
   __syncthreads();
   const int P = 1 << lgP, sh = A.cp.lgL - lgP;
-  for (int m = threadIdx.x; m < P; m += blockDim.x) S.tw[m] = __ldg(A.twL + (m << sh));
+  T *tw = static_cast<T *>(S.tw);
+  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = twG[m << sh];
   __syncthreads();
 }
 
@@ -69,28 +74,27 @@ __device__ __forceinline__ void my_items(int nitems, int &lo, int &hi) {
 // INV: line m2 loads Yin[k1*P2 + m2] * conj(W^{m2 k1}) and is inverse-transformed.
 // body(m, z) -> next forward input (z: inverse result when INV, otherwise undefined).
 // FWD: forward transform of body's outputs, twiddle W^{m2 k1}, store Yout[k1*P2 + m2].
-// W^{e} = twL[e << tws] (tws = 1 for the half-length conv plan, 0 for the length-L plan).
+// W^{e} = twG[e << tws] (tws = 1 for the half-length conv plan, 0 for the length-L plan).
 // ------------------------------------------------------------------------------------------------
-template <bool INV, bool FWD, class Body>
-__device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, int lg2, int tws,
-                                         int cap, const double2 *Yin, double2 *Yout,
-                                         Body body) {
+template <bool INV, bool FWD, typename T, class Body>
+__device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *twG, int lg1, int lg2,
+                                         int tws, int cap, const T *Yin, T *Yout, Body body) {
   const int P1 = 1 << lg1, P2 = 1 << lg2;
-  const double2 *__restrict__ tw = A.twL;
+  T *tw = static_cast<T *>(S.tw);
   int lo, hi;
   my_items(P2, lo, hi);
-  if (lo < hi) load_line_twiddles(A, S, lg1);
+  if (lo < hi) load_line_twiddles<T>(A, S, twG, lg1);
   for (int c0 = lo; c0 < hi; c0 += cap) {
     const int cnt = min(cap, hi - c0);
-    double2 *a = S.a, *b = S.b;
+    T *a = static_cast<T *>(S.a), *b = static_cast<T *>(S.b);
     if (INV) {
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
-        a[(l << lg1) + k1] = cmulc(Yin[(k1 << lg2) + m2], __ldg(tw + ((m2 * k1) << tws)));
+        a[(l << lg1) + k1] = cmulc(Yin[(k1 << lg2) + m2], twG[(m2 * k1) << tws]);
       }
       __syncthreads();
-      a = smem_fft<+1>(a, b, lg1, cnt, S.tw, lg1);
-      b = (a == S.a) ? S.b : S.a;
+      a = smem_fft<+1>(a, b, lg1, cnt, tw, lg1);
+      b = (a == static_cast<T *>(S.a)) ? static_cast<T *>(S.b) : static_cast<T *>(S.a);
     }
     for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
       const int l = e % cnt, m1 = e / cnt, m2 = c0 + l;
@@ -99,10 +103,10 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, 
     }
     __syncthreads();
     if (FWD) {
-      a = smem_fft<-1>(a, b, lg1, cnt, S.tw, lg1);
+      a = smem_fft<-1>(a, b, lg1, cnt, tw, lg1);
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
-        Yout[(k1 << lg2) + m2] = cmul(a[(l << lg1) + k1], __ldg(tw + ((m2 * k1) << tws)));
+        Yout[(k1 << lg2) + m2] = cmul(a[(l << lg1) + k1], twG[(m2 * k1) << tws]);
       }
       __syncthreads();
     }
@@ -116,9 +120,10 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, int lg1, 
 //   X_k = (E2 + w O2)/2, X_{k+N} = (E2 - w O2)/2, E2 = Z_k + conj Z_{N-k},
 //   O2 = -i (Z_k - conj Z_{N-k}), w = e^{-2 pi i k / L}.
 // MODE 0 (convolve): Y = S X at k and k+N (S_{k+N} = conj S_{N-k}, S_N stored at slot N), then
-//   the inverse split and the inverse row FFTs; result to Y2.  Spectra are pre-scaled by 1/(4N).
-// MODE 1 (spectrum): store X_k (times `scale`) into Sout at slot(k) and X_N at slot N, and, when
-//   sym != 0, also the spectra of A and B of level j at the same slots.
+//   the inverse split and the inverse row FFTs; result to Yout.  Spectra are pre-scaled 1/(4N).
+// MODE 1 (spectrum, FP64 only): store X_k (times `scale`) into Sout at slot(k) and X_N at slot
+//   N, and, when sym_level >= 0, also the spectra of A and B of that level at the same slots
+//   (plus their FP32 copies in the mixed mode).
 // ------------------------------------------------------------------------------------------------
 struct LevelScalars {
   double eta, q, kp, km;
@@ -145,39 +150,49 @@ __device__ __forceinline__ void ab_symbols(const Args &A, const LevelScalars &s,
   sb = make_double2((s.eta + (1.0 - A.sigma) * lre) * sc, ((1.0 - A.sigma) * lim) * sc);
 }
 
-template <int MODE>
-__device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const double2 *Sym,
-                                         double2 *Sout, double scale, int sym_level) {
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+__device__ __forceinline__ void store_ab(const Args &A, const LevelScalars &s, int slot, int k, bool nyq) {
+  double2 sa, sb;
+  ab_symbols(A, s, __ldg(A.twL + k), nyq, A.What[slot], sa, sb);
+  A.SA[slot] = sa;
+  A.SB[slot] = sb;
+  if (A.precision == kMixed) A.SA32[slot] = to_f2(sa);
+}
+
+template <int MODE, typename T>
+__device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *twG, const T *Yin, T *Yout,
+                                         const T *Sym, double2 *Sout, double scale, int sym_level) {
   const ConvPlan &P = A.cp;
   const int N1 = P.N1, N2 = P.N2, lg2 = P.lg2, N = P.N;
-  const double2 *__restrict__ tw = A.twL;
+  T *tw = static_cast<T *>(S.tw);
   const int nitems = N1 / 2 + 1;
   int lo, hi;
   my_items(nitems, lo, hi);
-  if (lo < hi) load_line_twiddles(A, S, lg2);
+  if (lo < hi) load_line_twiddles<T>(A, S, twG, lg2);
   LevelScalars ls;
   if (MODE == 1 && sym_level >= 0) ls = level_scalars(A, sym_level);
   for (int i0 = lo; i0 < hi; i0 += A.cap_row) {
     const int cnt = min(A.cap_row, hi - i0);
     const int nl = 2 * cnt;
-    double2 *a = S.a, *b = S.b;
+    T *a = static_cast<T *>(S.a), *b = static_cast<T *>(S.b);
     // load: line 2t = row ka, line 2t+1 = row kb
     for (int e = threadIdx.x; e < nl * N2; e += blockDim.x) {
       const int line = e >> lg2, k2 = e & (N2 - 1);
       const int it = i0 + (line >> 1);
       const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
-      a[e] = A.Y1[(row << lg2) + k2];
+      a[e] = Yin[(row << lg2) + k2];
     }
     __syncthreads();
-    a = smem_fft<-1>(a, b, lg2, nl, S.tw, lg2);
-    b = (a == S.a) ? S.b : S.a;
+    a = smem_fft<-1>(a, b, lg2, nl, tw, lg2);
+    b = (a == static_cast<T *>(S.a)) ? static_cast<T *>(S.b) : static_cast<T *>(S.a);
     // split / multiply / merge, pairwise in k and N-k
     for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
       const int t = e >> lg2, k2 = e & (N2 - 1);
       const int it = i0 + t;
       const int ka = it, kb = (N1 - it) & (N1 - 1);
-      double2 *ra = a + ((2 * t) << lg2);
-      double2 *rb = (ka == kb) ? ra : a + ((2 * t + 1) << lg2);
+      T *ra = a + ((2 * t) << lg2);
+      T *rb = (ka == kb) ? ra : a + ((2 * t + 1) << lg2);
       int k2p;
       if (ka == 0) {
         if (k2 > N2 / 2) continue;
@@ -189,57 +204,53 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const dou
         k2p = N2 - 1 - k2;
       }
       const int k = ka + N1 * k2;
-      const double2 Zk = ra[k2], Zp = rb[k2p];
-      const double2 w = __ldg(tw + k);
-      const double2 Zc = cconj(Zp);
-      const double2 E2 = cadd(Zk, Zc);
-      const double2 O2 = mul_mi(csub(Zk, Zc));
-      const double2 t2 = cmul(w, O2);
-      const double2 X0 = cadd(E2, t2), X1 = csub(E2, t2);
+      const T Zk = ra[k2], Zp = rb[k2p];
+      const T w = twG[k];
+      const T Zc = cconj(Zp);
+      const T E2 = cadd(Zk, Zc);
+      const T O2 = mul_mi(csub(Zk, Zc));
+      const T t2 = cmul(w, O2);
+      const T X0 = cadd(E2, t2), X1 = csub(E2, t2);
       const int sk = (ka << lg2) + k2, sp = (kb << lg2) + k2p;
       const bool self = (rb == ra) && (k2p == k2);
       if (MODE == 0) {
-        const double2 S0 = Sym[sk];
-        const double2 S1 = (k == 0) ? Sym[N] : cconj(Sym[sp]);
-        const double2 Y0 = cmul(S0, X0), Y1 = cmul(S1, X1);
-        const double2 Ep = cadd(Y0, Y1);
-        const double2 Op = cmulc(csub(Y0, Y1), w);
-        const double2 iOp = mul_i(Op);
+        const T S0 = Sym[sk];
+        const T S1 = (k == 0) ? Sym[N] : cconj(Sym[sp]);
+        const T Y0 = cmul(S0, X0), Y1 = cmul(S1, X1);
+        const T Ep = cadd(Y0, Y1);
+        const T Op = cmulc(csub(Y0, Y1), w);
+        const T iOp = mul_i(Op);
         ra[k2] = cadd(Ep, iOp);
         if (!self) rb[k2p] = cconj(csub(Ep, iOp));
       } else {
         const double sc = 0.5 * scale;
-        Sout[sk] = cscale(X0, sc);
-        if (!self) Sout[sp] = cscale(cconj(X1), sc);
-        if (k == 0) Sout[N] = cscale(X1, sc);
+        const double2 v0 = make_double2((double)X0.x * sc, (double)X0.y * sc);
+        const double2 v1 = make_double2((double)X1.x * sc, -(double)X1.y * sc);
+        const double2 vn = make_double2((double)X1.x * sc, (double)X1.y * sc);
+        Sout[sk] = v0;
+        if (!self) Sout[sp] = v1;
+        if (k == 0) Sout[N] = vn;
+        if (A.precision == kMixed && sym_level >= 0 && Sout == A.SP) {
+          A.SP32[sk] = to_f2(v0);
+          if (!self) A.SP32[sp] = to_f2(v1);
+          if (k == 0) A.SP32[N] = to_f2(vn);
+        }
         if (sym_level >= 0) {
-          double2 sa, sb;
-          ab_symbols(A, ls, w, false, A.What[sk], sa, sb);
-          A.SA[sk] = sa;
-          A.SB[sk] = sb;
-          if (!self) {
-            const int kpf = (N - k) & (N - 1);
-            ab_symbols(A, ls, __ldg(tw + kpf), false, A.What[sp], sa, sb);
-            A.SA[sp] = sa;
-            A.SB[sp] = sb;
-          }
-          if (k == 0) {
-            ab_symbols(A, ls, __ldg(tw + N), true, A.What[N], sa, sb);
-            A.SA[N] = sa;
-            A.SB[N] = sb;
-          }
+          store_ab(A, ls, sk, k, false);
+          if (!self) store_ab(A, ls, sp, (N - k) & (N - 1), false);
+          if (k == 0) store_ab(A, ls, N, N, true);
         }
       }
     }
     __syncthreads();
     if (MODE == 0) {
-      a = smem_fft<+1>(a, b, lg2, nl, S.tw, lg2);
+      a = smem_fft<+1>(a, b, lg2, nl, tw, lg2);
       for (int e = threadIdx.x; e < nl * N2; e += blockDim.x) {
         const int line = e >> lg2, k2 = e & (N2 - 1);
         const int it = i0 + (line >> 1);
         const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
         if ((line & 1) && row == it) continue;   // self-paired row stored once
-        A.Y2[(row << lg2) + k2] = a[e];
+        Yout[(row << lg2) + k2] = a[e];
       }
       __syncthreads();
     }
@@ -247,28 +258,29 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const dou
 }
 
 // ------------------------------------------------------------------------------------------------
-// Row pass of the length-L complex plan (Bluestein): forward row FFT, then either multiply by
-// Tab (permuted) and inverse row FFT into Y2 (MODE 0) or store the spectrum * scale (MODE 1).
+// Row pass of the length-L complex plan (Bluestein), FP64: forward row FFT, then either multiply
+// by Tab (permuted) and inverse row FFT into Y2 (MODE 0) or store the spectrum * scale (MODE 1).
 // ------------------------------------------------------------------------------------------------
 template <int MODE>
 __device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const double2 *Tab,
                                           double2 *Out, double scale) {
   const CplxPlan &P = A.bp;
   const int lg2 = P.lg2, N2 = P.N2;
+  double2 *tw = static_cast<double2 *>(S.tw);
   int lo, hi;
   my_items(P.N1, lo, hi);
-  if (lo < hi) load_line_twiddles(A, S, lg2);
+  if (lo < hi) load_line_twiddles<double2>(A, S, A.twL, lg2);
   for (int r0 = lo; r0 < hi; r0 += A.cap_brow) {
     const int cnt = min(A.cap_brow, hi - r0);
-    double2 *a = S.a, *b = S.b;
+    double2 *a = static_cast<double2 *>(S.a), *b = static_cast<double2 *>(S.b);
     for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = A.Y1[(r0 << lg2) + e];
     __syncthreads();
-    a = smem_fft<-1>(a, b, lg2, cnt, S.tw, lg2);
-    b = (a == S.a) ? S.b : S.a;
+    a = smem_fft<-1>(a, b, lg2, cnt, tw, lg2);
+    b = (a == static_cast<double2 *>(S.a)) ? static_cast<double2 *>(S.b) : static_cast<double2 *>(S.a);
     if (MODE == 0) {
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = cmul(a[e], Tab[(r0 << lg2) + e]);
       __syncthreads();
-      a = smem_fft<+1>(a, b, lg2, cnt, S.tw, lg2);
+      a = smem_fft<+1>(a, b, lg2, cnt, tw, lg2);
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) A.Y2[(r0 << lg2) + e] = a[e];
     } else {
       for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) Out[(r0 << lg2) + e] = cscale(a[e], scale);
@@ -321,50 +333,58 @@ __device__ __forceinline__ void read_partials(const Args &A, const Smem &S, int 
   tot[2] = v[2];
 }
 
+template <typename T>
+__device__ __forceinline__ T ldp(const typename RealOf<T>::R *v, int m) { return reinterpret_cast<const T *>(v)[m]; }
+template <typename T>
+__device__ __forceinline__ void stp(typename RealOf<T>::R *v, int m, T z) { reinterpret_cast<T *>(v)[m] = z; }
+__device__ __forceinline__ double2 ld2(const double *v, int m) { return reinterpret_cast<const double2 *>(v)[m]; }
+__device__ __forceinline__ void st2(double *v, int m, double2 z) { reinterpret_cast<double2 *>(v)[m] = z; }
+
 // ------------------------------------------------------------------------------------------------
-// phases
+// phases of the level symbols
 // ------------------------------------------------------------------------------------------------
 
 // Bluestein, inverse n-point DFT of 1/Lambda_P (first column of P^{-1}), phase 1 of 3.
 __device__ void ph_pinv_b1(const Args &A, const Smem &S, int j) {
   const LevelScalars s = level_scalars(A, j);
   const int n = A.n;
-  col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
-                        [&](int m, double2) -> double2 {
-                          if (m >= n) return make_double2(0.0, 0.0);
-                          const double2 lp = lambda_p(A, s, m);
-                          const double d = lp.x * lp.x + lp.y * lp.y;
-                          if (!(d > 0.0) || !isfinite(d)) raise_fatal(A, kESingular);
-                          const double2 inv = make_double2(lp.x / d, -lp.y / d);
-                          return cmul(inv, A.chirpI[m]);
-                        });
+  col_pass<false, true, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 {
+                                   if (m >= n) return make_double2(0.0, 0.0);
+                                   const double2 lp = lambda_p(A, s, m);
+                                   const double d = lp.x * lp.x + lp.y * lp.y;
+                                   if (!(d > 0.0) || !isfinite(d)) raise_fatal(A, kESingular);
+                                   const double2 inv = make_double2(lp.x / d, -lp.y / d);
+                                   return cmul(inv, A.chirpI[m]);
+                                 });
 }
 __device__ void ph_pinv_b2(const Args &A, const Smem &S) { crow_pass<0>(A, S, A.BhI, nullptr, 1.0); }
 __device__ void ph_pinv_b3(const Args &A, const Smem &S) {
   const int n = A.n;
-  col_pass<true, false>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
-                        [&](int m, double2 z) -> double2 {
-                          if (m < n) A.cprime[m] = cmul(z, A.chirpI[m]).x;
-                          return z;
-                        });
+  col_pass<true, false, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
+                                 [&](int m, double2 z) -> double2 {
+                                   if (m < n) A.cprime[m] = cmul(z, A.chirpI[m]).x;
+                                   return z;
+                                 });
 }
 // Toeplitz embedding of the circulant P^{-1} (entries t_d = c'_{d mod n}) and its column FFT.
 __device__ void ph_pinv_c1(const Args &A, const Smem &S) {
   const int n = A.n, L = A.cp.L;
-  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                        [&](int m, double2) -> double2 {
-                          double v[2];
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
 #pragma unroll
-                          for (int h = 0; h < 2; ++h) {
-                            const int i = 2 * m + h;
-                            v[h] = i < n ? A.cprime[i] : (i > L - n ? A.cprime[i + n - L] : 0.0);   // t_{-d} = c'_{n-d}
-                          }
-                          return make_double2(v[0], v[1]);
-                        });
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     // t_{-d} = c'_{n-d}
+                                     v[h] = i < n ? A.cprime[i] : (i > L - n ? A.cprime[i + n - L] : 0.0);
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
 }
 // Spectrum of P^{-1}'s embedding, plus A and B of level j.
 __device__ void ph_pinv_c2(const Args &A, const Smem &S, int j) {
-  row_pass<1>(A, S, nullptr, A.SP, 1.0 / (4.0 * (double)A.cp.N), j);
+  row_pass<1, double2>(A, S, A.twL, A.Y1, nullptr, nullptr, A.SP, 1.0 / (4.0 * (double)A.cp.N), j);
 }
 // A and B spectra only (no preconditioner).
 __device__ void ph_ab_only(const Args &A, const Smem &S, int j) {
@@ -372,11 +392,26 @@ __device__ void ph_ab_only(const Args &A, const Smem &S, int j) {
   const ConvPlan &P = A.cp;
   for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl <= P.N; sl += gridDim.x * blockDim.x) {
     const int k = sl == P.N ? P.N : ((sl & (P.N2 - 1)) * P.N1 + (sl >> P.lg2));
-    double2 sa, sb;
-    ab_symbols(A, s, __ldg(A.twL + k), sl == P.N, A.What[sl], sa, sb);
-    A.SA[sl] = sa;
-    A.SB[sl] = sb;
+    store_ab(A, s, sl, k, sl == P.N);
   }
+}
+
+// Symbols for level j (preconditioned or not).  Returns false if aborted.
+__device__ bool level_symbols(const Args &A, const Smem &S, int j) {
+  if (A.precond != 2) {
+    ph_pinv_b1(A, S, j);
+    if (!grid_sync(A)) return false;
+    ph_pinv_b2(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_b3(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_c1(A, S);
+    if (!grid_sync(A)) return false;
+    ph_pinv_c2(A, S, j);
+  } else {
+    ph_ab_only(A, S, j);
+  }
+  return grid_sync(A);
 }
 
 // Commit of level j-1 (when commit), history sum of Lemma 1 for level j into H, contiguous.
@@ -435,25 +470,158 @@ __device__ void ph_commit(const Args &A, int j) {
   }
 }
 
-__device__ __forceinline__ double2 ld2(const double *v, int m) { return reinterpret_cast<const double2 *>(v)[m]; }
-__device__ __forceinline__ void st2(double *v, int m, double2 z) { reinterpret_cast<double2 *>(v)[m] = z; }
+// ------------------------------------------------------------------------------------------------
+// Preconditioned CGS (Section 4; Barrett et al. "Templates" form) on A d = b in element type T,
+// from the current iterate x with r = b - A x, r~ = u = p = r already stored, rho = (r~, r).
+// The forward column transform of p is already in Y1 when fwd_done.  Stops when
+// ||r_k|| < tol * nref (nref = ||r_0|| for a plain solve) or after maxit iterations.
+// Returns the status; `its` and `rel` (= ||r_k|| / nref) are set; `alive` is false if the
+// kernel must stop.  Every CTA takes the same decisions (identical reduced scalars).  Dot
+// products accumulate per thread in T's precision and are reduced across the grid in FP64.
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+struct Krylov {
+  typename RealOf<T>::R *x, *r, *rt, *p, *q, *uu, *vh;
+  const T *SA, *SP;
+  T *Y1, *Y2;
+  const T *twG;
+};
 
-// Symbols for level j (precondition or not).  Returns false if aborted.
-__device__ bool level_symbols(const Args &A, const Smem &S, int j) {
-  if (A.precond != 2) {
-    ph_pinv_b1(A, S, j);
-    if (!grid_sync(A)) return false;
-    ph_pinv_b2(A, S);
-    if (!grid_sync(A)) return false;
-    ph_pinv_b3(A, S);
-    if (!grid_sync(A)) return false;
-    ph_pinv_c1(A, S);
-    if (!grid_sync(A)) return false;
-    ph_pinv_c2(A, S, j);
-  } else {
-    ph_ab_only(A, S, j);
+template <typename T>
+__device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, double rho, double nref,
+                         double tol, int maxit, bool fwd_done, int &rb, int &its, double &rel,
+                         bool &alive) {
+  using R = typename RealOf<T>::R;
+  const int n = A.n;
+  const bool pc = A.precond != 2;
+  its = 0;
+  rel = 0.0;
+  alive = true;
+  if (!(nref > 0.0)) return kOK;
+  if (!fwd_done) {
+    col_pass<false, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, V.Y1,
+                             [&](int m, T) -> T { return ldp<T>(V.p, m); });
+    if (!(alive = grid_sync(A))) return kOK;
   }
-  return grid_sync(A);
+  double tot[3];
+  bool first = true;
+  double beta = 0.0;
+  while (true) {
+    ++its;
+    if (!first) {
+      const R bt = (R)beta;
+      // u = r + beta q; p = u + beta (q + beta p); forward transform of p
+      col_pass<false, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, V.Y1,
+                               [&](int m, T) -> T {
+                                 const T rv = ldp<T>(V.r, m), qv = ldp<T>(V.q, m), pv = ldp<T>(V.p, m);
+                                 T uv, pn;
+                                 mkc(uv, rv.x + bt * qv.x, rv.y + bt * qv.y);
+                                 mkc(pn, uv.x + bt * (qv.x + bt * pv.x), uv.y + bt * (qv.y + bt * pv.y));
+                                 stp<T>(V.uu, m, uv);
+                                 stp<T>(V.p, m, pn);
+                                 return pn;
+                               });
+      if (!(alive = grid_sync(A))) return kOK;
+    }
+    first = false;
+    if (pc) {   // p^ = P^{-1} p
+      row_pass<0, T>(A, S, V.twG, V.Y1, V.Y2, V.SP, nullptr, 0.0, -1);
+      if (!(alive = grid_sync(A))) return kOK;
+      col_pass<true, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, V.Y2, V.Y1,
+                              [&](int m, T z) -> T {
+                                if (2 * m >= n) z.x = (R)0;
+                                if (2 * m + 1 >= n) z.y = (R)0;
+                                return z;
+                              });
+      if (!(alive = grid_sync(A))) return kOK;
+    }
+    // v^ = A p^, sigma = (r~, v^)
+    row_pass<0, T>(A, S, V.twG, V.Y1, V.Y2, V.SA, nullptr, 0.0, -1);
+    if (!(alive = grid_sync(A))) return kOK;
+    {
+      R a0 = (R)0;
+      col_pass<true, false, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, V.Y2, nullptr,
+                               [&](int m, T z) -> T {
+                                 if (2 * m >= n) z.x = (R)0;
+                                 if (2 * m + 1 >= n) z.y = (R)0;
+                                 stp<T>(V.vh, m, z);
+                                 const T rtv = ldp<T>(V.rt, m);
+                                 a0 += rtv.x * z.x + rtv.y * z.y;
+                                 return z;
+                               });
+      double acc[3] = {(double)a0, 0.0, 0.0};
+      write_partials(A, S, rb, acc);
+    }
+    if (!(alive = grid_sync(A))) return kOK;
+    read_partials(A, S, rb, tot);
+    rb ^= 1;
+    const double sig = tot[0];
+    if (sig == 0.0) return kEBreakdown;
+    if (!(sig == sig) || isinf(sig)) return kENonFinite;
+    const R alpha = (R)(rho / sig);
+    // q = u - alpha v^; w = u + q; forward transform of w (x += alpha w when unpreconditioned)
+    col_pass<false, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, V.Y1,
+                             [&](int m, T) -> T {
+                               const T uv = ldp<T>(V.uu, m), vv = ldp<T>(V.vh, m);
+                               T qv, wv;
+                               mkc(qv, uv.x - alpha * vv.x, uv.y - alpha * vv.y);
+                               mkc(wv, uv.x + qv.x, uv.y + qv.y);
+                               stp<T>(V.q, m, qv);
+                               if (!pc) {
+                                 const T xv = ldp<T>(V.x, m);
+                                 T xn;
+                                 mkc(xn, xv.x + alpha * wv.x, xv.y + alpha * wv.y);
+                                 stp<T>(V.x, m, xn);
+                               }
+                               return wv;
+                             });
+    if (!(alive = grid_sync(A))) return kOK;
+    if (pc) {   // u^ = P^{-1} w; x += alpha u^
+      row_pass<0, T>(A, S, V.twG, V.Y1, V.Y2, V.SP, nullptr, 0.0, -1);
+      if (!(alive = grid_sync(A))) return kOK;
+      col_pass<true, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, V.Y2, V.Y1,
+                              [&](int m, T z) -> T {
+                                if (2 * m >= n) z.x = (R)0;
+                                if (2 * m + 1 >= n) z.y = (R)0;
+                                const T xv = ldp<T>(V.x, m);
+                                T xn;
+                                mkc(xn, xv.x + alpha * z.x, xv.y + alpha * z.y);
+                                stp<T>(V.x, m, xn);
+                                return z;
+                              });
+      if (!(alive = grid_sync(A))) return kOK;
+    }
+    // r -= alpha A u^; rho' = (r~, r), ||r||^2
+    row_pass<0, T>(A, S, V.twG, V.Y1, V.Y2, V.SA, nullptr, 0.0, -1);
+    if (!(alive = grid_sync(A))) return kOK;
+    {
+      R a0 = (R)0, a1 = (R)0;
+      col_pass<true, false, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, V.Y2, nullptr,
+                               [&](int m, T z) -> T {
+                                 if (2 * m >= n) z.x = (R)0;
+                                 if (2 * m + 1 >= n) z.y = (R)0;
+                                 const T rv = ldp<T>(V.r, m), rtv = ldp<T>(V.rt, m);
+                                 T rn;
+                                 mkc(rn, rv.x - alpha * z.x, rv.y - alpha * z.y);
+                                 stp<T>(V.r, m, rn);
+                                 a0 += rtv.x * rn.x + rtv.y * rn.y;
+                                 a1 += rn.x * rn.x + rn.y * rn.y;
+                                 return z;
+                               });
+      double acc[3] = {(double)a0, (double)a1, 0.0};
+      write_partials(A, S, rb, acc);
+    }
+    if (!(alive = grid_sync(A))) return kOK;
+    read_partials(A, S, rb, tot);
+    rb ^= 1;
+    rel = sqrt(tot[1]) / nref;
+    if (!(rel == rel) || isinf(rel)) return kENonFinite;
+    if (rel < tol) return kOK;
+    if (its >= maxit) return kENotConverged;
+    if (tot[0] == 0.0) return kEBreakdown;
+    beta = tot[0] / rho;
+    rho = tot[0];
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -463,8 +631,15 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
   const int n = A.n;
-  const bool pc = A.precond != 2;
+  const bool mixed = A.precision == kMixed;
   int rb = 0;
+  Krylov<double2> V64;
+  V64.x = A.x; V64.r = A.r; V64.rt = A.rt; V64.p = A.p; V64.q = A.q; V64.uu = A.uu; V64.vh = A.vh;
+  V64.SA = A.SA; V64.SP = A.SP; V64.Y1 = A.Y1; V64.Y2 = A.Y2; V64.twG = A.twL;
+  Krylov<float2> V32;
+  V32.x = A.x32; V32.r = A.r32; V32.rt = A.rt32; V32.p = A.p32; V32.q = A.q32; V32.uu = A.uu32;
+  V32.vh = A.vh32; V32.SA = A.SA32; V32.SP = A.SP32; V32.Y1 = A.Y1f; V32.Y2 = A.Y2f; V32.twG = A.twL32;
+
   for (int j = j0; j < j1; ++j) {
     if (j == j0 || A.lv_newsym[j]) {
       if (!level_symbols(A, S, j)) return;
@@ -474,155 +649,139 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
     ph_history(A, j, commit);
     {
       const double *src = commit ? A.x : A.u;
-      col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                            [&](int m, double2) -> double2 { return ld2(src, m); });
+      col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                     [&](int m, double2) -> double2 { return ld2(src, m); });
     }
     if (!grid_sync(A)) return;
-    row_pass<0>(A, S, A.SB, nullptr, 0.0, -1);
+    row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, A.SB, nullptr, 0.0, -1);
     if (!grid_sync(A)) return;
     double acc[3] = {0.0, 0.0, 0.0};
-    col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
-                         [&](int m, double2 y) -> double2 {
-                           double gv[2] = {y.x, y.y};
-                           const double2 hv = ld2(A.H, m);
-                           const double hh[2] = {hv.x, hv.y};
+    // plain: x = 0, r = r~ = u = p = g and the forward transform of p fused here;
+    // mixed: g kept in FP64, x = 0, r = g, and the FP32 inner start r32 = r~32 = u32 = p32 = g
+    col_pass<true, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                                  [&](int m, double2 y) -> double2 {
+                                    double gv[2] = {y.x, y.y};
+                                    const double2 hv = ld2(A.H, m);
+                                    const double hh[2] = {hv.x, hv.y};
 #pragma unroll
-                           for (int h = 0; h < 2; ++h) {
-                             const int i = 2 * m + h;
-                             if (i < n) {
-                               gv[h] = gv[h] - A.hscale * hh[h] + source_at(A, j, i);
-                               acc[0] += gv[h] * gv[h];
-                             } else {
-                               gv[h] = 0.0;
-                             }
-                           }
-                           const double2 g = make_double2(gv[0], gv[1]);
-                           st2(A.x, m, make_double2(0.0, 0.0));
-                           st2(A.r, m, g);
-                           st2(A.rt, m, g);
-                           st2(A.uu, m, g);
-                           st2(A.p, m, g);
-                           return g;
-                         });
+                                    for (int h = 0; h < 2; ++h) {
+                                      const int i = 2 * m + h;
+                                      if (i < n) {
+                                        gv[h] = gv[h] - A.hscale * hh[h] + source_at(A, j, i);
+                                        acc[0] += gv[h] * gv[h];
+                                      } else {
+                                        gv[h] = 0.0;
+                                      }
+                                    }
+                                    const double2 g = make_double2(gv[0], gv[1]);
+                                    st2(A.x, m, make_double2(0.0, 0.0));
+                                    st2(A.r, m, g);
+                                    if (mixed) {
+                                      st2(A.g, m, g);
+                                      const float2 g32 = to_f2(g);
+                                      stp<float2>(A.x32, m, make_float2(0.f, 0.f));
+                                      stp<float2>(A.r32, m, g32);
+                                      stp<float2>(A.rt32, m, g32);
+                                      stp<float2>(A.uu32, m, g32);
+                                      stp<float2>(A.p32, m, g32);
+                                      acc[1] += (double)(g32.x * g32.x + g32.y * g32.y);
+                                    } else {
+                                      st2(A.rt, m, g);
+                                      st2(A.uu, m, g);
+                                      st2(A.p, m, g);
+                                    }
+                                    return g;
+                                  });
     write_partials(A, S, rb, acc);
     if (!grid_sync(A)) return;
     double tot[3];
     read_partials(A, S, rb, tot);
     rb ^= 1;
-    double rho = tot[0];
-    const double nr0 = sqrt(tot[0]);
-    int it = 0;
+    const double gnorm = sqrt(tot[0]);
+    int lstat = kOK, its = 0, outer = 0, esc = 0;
     double rel = 0.0;
-    int lstat = kOK;
-    if (!(nr0 == nr0) || isinf(nr0)) lstat = kENonFinite;
-    bool first = true;
-    double beta = 0.0;
-    while (lstat == kOK && nr0 > 0.0) {
-      ++it;
-      if (!first) {
-        // u = r + beta q; p = u + beta (q + beta p); forward transform of p
-        col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                              [&](int m, double2) -> double2 {
-                                const double2 rv = ld2(A.r, m), qv = ld2(A.q, m), pv = ld2(A.p, m);
-                                const double2 uv = make_double2(rv.x + beta * qv.x, rv.y + beta * qv.y);
-                                const double2 pn = make_double2(uv.x + beta * (qv.x + beta * pv.x),
-                                                                uv.y + beta * (qv.y + beta * pv.y));
-                                st2(A.uu, m, uv);
-                                st2(A.p, m, pn);
-                                return pn;
-                              });
+    bool alive = true;
+    if (!(gnorm == gnorm) || isinf(gnorm)) {
+      lstat = kENonFinite;
+    } else if (!mixed) {
+      lstat = cgs_solve<double2>(A, S, V64, tot[0], gnorm, A.tol, A.maxit, true, rb, its, rel, alive);
+      if (!alive) return;
+    } else if (gnorm > 0.0) {
+      // iterative refinement: FP32 CGS on A d = r, x += d and r = g - A x in FP64
+      double rho32 = tot[1];
+      double prev = 1.0;
+      while (true) {
+        int ii = 0;
+        double irel = 0.0;
+        const int ist = cgs_solve<float2>(A, S, V32, rho32, sqrt(rho32), A.inner_tol, A.inner_maxit,
+                                          false, rb, ii, irel, alive);
+        if (!alive) return;
+        its += ii;
+        ++outer;
+        const bool inner_ok = ist == kOK || ist == kENotConverged;
+        // x += d (FP64); forward transform of x
+        col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                       [&](int m, double2) -> double2 {
+                                         double2 xv = ld2(A.x, m);
+                                         if (inner_ok) {
+                                           const float2 dv = ldp<float2>(A.x32, m);
+                                           xv = make_double2(xv.x + (double)dv.x, xv.y + (double)dv.y);
+                                           st2(A.x, m, xv);
+                                         }
+                                         return xv;
+                                       });
         if (!grid_sync(A)) return;
+        row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, A.SA, nullptr, 0.0, -1);
+        if (!grid_sync(A)) return;
+        // r = g - A x (FP64); restart values for the next inner solve (FP32) or the FP64 CGS
+        acc[0] = acc[1] = acc[2] = 0.0;
+        col_pass<true, false, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                                       [&](int m, double2 z) -> double2 {
+                                         const double2 gv = ld2(A.g, m);
+                                         double2 rv = make_double2(gv.x - z.x, gv.y - z.y);
+                                         if (2 * m >= n) rv.x = 0.0;
+                                         if (2 * m + 1 >= n) rv.y = 0.0;
+                                         acc[0] += rv.x * rv.x + rv.y * rv.y;
+                                         st2(A.r, m, rv);
+                                         st2(A.rt, m, rv);
+                                         st2(A.uu, m, rv);
+                                         st2(A.p, m, rv);
+                                         const float2 r32 = to_f2(rv);
+                                         stp<float2>(A.x32, m, make_float2(0.f, 0.f));
+                                         stp<float2>(A.r32, m, r32);
+                                         stp<float2>(A.rt32, m, r32);
+                                         stp<float2>(A.uu32, m, r32);
+                                         stp<float2>(A.p32, m, r32);
+                                         acc[1] += (double)(r32.x * r32.x + r32.y * r32.y);
+                                         return z;
+                                       });
+        write_partials(A, S, rb, acc);
+        if (!grid_sync(A)) return;
+        read_partials(A, S, rb, tot);
+        rb ^= 1;
+        rel = sqrt(tot[0]) / gnorm;
+        rho32 = tot[1];
+        if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
+        if (rel < A.tol) break;
+        // no progress (or diverging) in FP32 -> finish the level with the FP64 CGS from x
+        if (!inner_ok || rel > 0.5 * prev || outer >= A.outer_maxit) {
+          esc = 1;
+          int i64 = 0;
+          lstat = cgs_solve<double2>(A, S, V64, tot[0], gnorm, A.tol, A.maxit, false, rb, i64, rel, alive);
+          if (!alive) return;
+          its += i64;
+          break;
+        }
+        prev = rel;
       }
-      first = false;
-      if (pc) {   // p^ = P^{-1} p
-        row_pass<0>(A, S, A.SP, nullptr, 0.0, -1);
-        if (!grid_sync(A)) return;
-        col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
-                             [&](int m, double2 z) -> double2 {
-                               if (2 * m >= n) z.x = 0.0;
-                               if (2 * m + 1 >= n) z.y = 0.0;
-                               return z;
-                             });
-        if (!grid_sync(A)) return;
-      }
-      // v^ = A p^, sigma = (r~, v^)
-      row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
-      if (!grid_sync(A)) return;
-      acc[0] = acc[1] = acc[2] = 0.0;
-      col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
-                            [&](int m, double2 z) -> double2 {
-                              if (2 * m >= n) z.x = 0.0;
-                              if (2 * m + 1 >= n) z.y = 0.0;
-                              st2(A.vh, m, z);
-                              const double2 rtv = ld2(A.rt, m);
-                              acc[0] += rtv.x * z.x + rtv.y * z.y;
-                              return z;
-                            });
-      write_partials(A, S, rb, acc);
-      if (!grid_sync(A)) return;
-      read_partials(A, S, rb, tot);
-      rb ^= 1;
-      const double sig = tot[0];
-      if (sig == 0.0) { lstat = kEBreakdown; break; }
-      if (!(sig == sig) || isinf(sig)) { lstat = kENonFinite; break; }
-      const double alpha = rho / sig;
-      // q = u - alpha v^; w = u + q; forward transform of w (x += alpha w when unpreconditioned)
-      col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                            [&](int m, double2) -> double2 {
-                              const double2 uv = ld2(A.uu, m), vv = ld2(A.vh, m);
-                              const double2 qv = make_double2(uv.x - alpha * vv.x, uv.y - alpha * vv.y);
-                              const double2 wv = make_double2(uv.x + qv.x, uv.y + qv.y);
-                              st2(A.q, m, qv);
-                              if (!pc) {
-                                const double2 xv = ld2(A.x, m);
-                                st2(A.x, m, make_double2(xv.x + alpha * wv.x, xv.y + alpha * wv.y));
-                              }
-                              return wv;
-                            });
-      if (!grid_sync(A)) return;
-      if (pc) {   // u^ = P^{-1} w; x += alpha u^
-        row_pass<0>(A, S, A.SP, nullptr, 0.0, -1);
-        if (!grid_sync(A)) return;
-        col_pass<true, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
-                             [&](int m, double2 z) -> double2 {
-                               if (2 * m >= n) z.x = 0.0;
-                               if (2 * m + 1 >= n) z.y = 0.0;
-                               const double2 xv = ld2(A.x, m);
-                               st2(A.x, m, make_double2(xv.x + alpha * z.x, xv.y + alpha * z.y));
-                               return z;
-                             });
-        if (!grid_sync(A)) return;
-      }
-      // r -= alpha A u^; rho' = (r~, r), ||r||^2
-      row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
-      if (!grid_sync(A)) return;
-      acc[0] = acc[1] = acc[2] = 0.0;
-      col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
-                            [&](int m, double2 z) -> double2 {
-                              if (2 * m >= n) z.x = 0.0;
-                              if (2 * m + 1 >= n) z.y = 0.0;
-                              const double2 rv = ld2(A.r, m), rtv = ld2(A.rt, m);
-                              const double2 rn = make_double2(rv.x - alpha * z.x, rv.y - alpha * z.y);
-                              st2(A.r, m, rn);
-                              acc[0] += rtv.x * rn.x + rtv.y * rn.y;
-                              acc[1] += rn.x * rn.x + rn.y * rn.y;
-                              return z;
-                            });
-      write_partials(A, S, rb, acc);
-      if (!grid_sync(A)) return;
-      read_partials(A, S, rb, tot);
-      rb ^= 1;
-      rel = sqrt(tot[1]) / nr0;
-      if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
-      if (rel < A.tol) break;
-      if (it >= A.maxit) { lstat = kENotConverged; break; }
-      if (tot[0] == 0.0) { lstat = kEBreakdown; break; }
-      beta = tot[0] / rho;
-      rho = tot[0];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      A.iters[j] = it;
+      A.iters[j] = its;
       A.resid[j] = rel;
+      if (mixed) {
+        A.outer_iters[j] = outer;
+        A.escalated[j] = esc;
+      }
       if (lstat != kOK) {
         atomicCAS(A.status, 0, lstat);
         if (lstat != kENotConverged) atomicExch(A.status + 1, 1);
@@ -642,18 +801,18 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int 
   grid_sync_init();
   const int n = A.n;
   if (!level_symbols(A, S, j)) return;
-  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                        [&](int m, double2) -> double2 { return ld2(xin, m); });
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 { return ld2(xin, m); });
   if (!grid_sync(A)) return;
-  row_pass<0>(A, S, op == 0 ? A.SA : (op == 1 ? A.SB : A.SP), nullptr, 0.0, -1);
+  row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, op == 0 ? A.SA : (op == 1 ? A.SB : A.SP), nullptr, 0.0, -1);
   if (!grid_sync(A)) return;
-  col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
-                        [&](int m, double2 z) -> double2 {
-                          if (2 * m >= n) z.x = 0.0;
-                          if (2 * m + 1 >= n) z.y = 0.0;
-                          st2(yout, m, z);
-                          return z;
-                        });
+  col_pass<true, false, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+                                 [&](int m, double2 z) -> double2 {
+                                   if (2 * m >= n) z.x = 0.0;
+                                   if (2 * m + 1 >= n) z.y = 0.0;
+                                   st2(yout, m, z);
+                                   return z;
+                                 });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -682,11 +841,12 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
   grid_sync_init();
   const int n = A.n, L = A.cp.L;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  // tables: twiddles e^{-2 pi i k/L}, chirp e^{i pi (k^2 mod 2n)/n}
+  // tables: twiddles e^{-2 pi i k/L} (and their FP32 copy), chirp e^{i pi (k^2 mod 2n)/n}
   for (int k = gt; k < L; k += gs) {
     double s, c;
     sincospi(-2.0 * (double)k / (double)L, &s, &c);
     T.twL[k] = make_double2(c, s);
+    if (A.precision == kMixed) A.twL32[k] = make_float2((float)c, (float)s);
   }
   for (int k = gt; k < n; k += gs) {
     const long long k2 = ((long long)k * (long long)k) % (2ll * n);
@@ -696,29 +856,29 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
   }
   if (!grid_sync(A)) return;
   // spectrum of the L-embedding of W_beta: t_0 = omega_1 ... t_{n-1} = omega_n, t_{-1} = omega_0
-  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
-                        [&](int m, double2) -> double2 {
-                          double v[2];
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
 #pragma unroll
-                          for (int h = 0; h < 2; ++h) {
-                            const int i = 2 * m + h;
-                            v[h] = i < n ? T.omega[i + 1] : (i == L - 1 ? T.omega[0] : 0.0);
-                          }
-                          return make_double2(v[0], v[1]);
-                        });
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     v[h] = i < n ? T.omega[i + 1] : (i == L - 1 ? T.omega[0] : 0.0);
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
   if (!grid_sync(A)) return;
-  row_pass<1>(A, S, nullptr, T.What, 1.0, -1);
+  row_pass<1, double2>(A, S, A.twL, A.Y1, nullptr, nullptr, T.What, 1.0, -1);
   if (!grid_sync(A)) return;
   // Bluestein kernels: b_d = e^{-+ i pi d^2/n} placed circularly (|d| < n), spectra scaled for
   // the inverse (1/(L n)) and forward (1/L) n-point DFTs.
   for (int pass = 0; pass < 2; ++pass) {
-    col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
-                          [&](int m, double2) -> double2 {
-                            int d = m < n ? m : (m > L - n ? L - m : -1);
-                            if (d < 0) return make_double2(0.0, 0.0);
-                            const double2 c = T.chirpI[d];
-                            return pass == 0 ? cconj(c) : c;
-                          });
+    col_pass<false, true, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                                   [&](int m, double2) -> double2 {
+                                     int d = m < n ? m : (m > L - n ? L - m : -1);
+                                     if (d < 0) return make_double2(0.0, 0.0);
+                                     const double2 c = T.chirpI[d];
+                                     return pass == 0 ? cconj(c) : c;
+                                   });
     if (!grid_sync(A)) return;
     crow_pass<1>(A, S, nullptr, pass == 0 ? T.BhI : T.BhF,
                  pass == 0 ? 1.0 / ((double)L * (double)n) : 1.0 / (double)L);
@@ -726,26 +886,21 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
   }
   // eigenvalues of s(W_beta) and s(Q): forward n-point DFT by Bluestein
   for (int which = 0; which < 2; ++which) {
-    col_pass<false, true>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
-                          [&](int m, double2) -> double2 {
-                            if (m >= n) return make_double2(0.0, 0.0);
-                            const double c = circ_col(T.omega, which, T.precond, n, m);
-                            return cscale(cconj(T.chirpI[m]), c);
-                          });
+    col_pass<false, true, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
+                                   [&](int m, double2) -> double2 {
+                                     if (m >= n) return make_double2(0.0, 0.0);
+                                     const double c = circ_col(T.omega, which, T.precond, n, m);
+                                     return cscale(cconj(T.chirpI[m]), c);
+                                   });
     if (!grid_sync(A)) return;
-    // reuse crow_pass<0> with the forward kernel
-    {
-      Args B = A;
-      B.BhI = T.BhF;
-      crow_pass<0>(B, S, T.BhF, nullptr, 1.0);
-    }
+    crow_pass<0>(A, S, T.BhF, nullptr, 1.0);
     if (!grid_sync(A)) return;
     double2 *out = which == 0 ? T.LamW : T.LamQ;
-    col_pass<true, false>(A, S, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
-                          [&](int m, double2 z) -> double2 {
-                            if (m < n) out[m] = cmulc(z, T.chirpI[m]);
-                            return z;
-                          });
+    col_pass<true, false, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
+                                   [&](int m, double2 z) -> double2 {
+                                     if (m < n) out[m] = cmulc(z, T.chirpI[m]);
+                                     return z;
+                                   });
     if (!grid_sync(A)) return;
   }
 }
@@ -753,15 +908,20 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
 // ------------------------------------------------------------------------------------------------
 // weights and per-level tables (Lemma 1, Lemma 2)
 // ------------------------------------------------------------------------------------------------
-// omega_k for k = 0..n+1: Grunwald recurrence g_k = (1 - (beta+1)/k) g_{k-1} (Lemma 3) run by
-// one thread with explicit rounding (no contraction), then the WSGD combination (Lemma 2).
-__global__ void grunwald_kernel(double *g, int K, double beta) {
+// omega_k for k = 0..n+1: the Grunwald recurrence g_k = (1 - (beta+1)/k) g_{k-1} (Lemma 3) with
+// explicit rounding (no contraction): factors in parallel, the running product by one thread;
+// then the WSGD combination (Lemma 2).
+__global__ void grunwald_factors_kernel(double *f, int K, double beta) {
+  for (int k = 1 + blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x)
+    f[k] = __dadd_rn(1.0, -__ddiv_rn(beta + 1.0, (double)k));
+}
+
+__global__ void grunwald_kernel(double *g, const double *f, int K) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double gk = 1.0;
     g[0] = gk;
     for (int k = 1; k <= K; ++k) {
-      const double f = __dadd_rn(1.0, -__ddiv_rn(beta + 1.0, (double)k));
-      gk = __dmul_rn(f, gk);
+      gk = __dmul_rn(f[k], gk);
       g[k] = gk;
     }
   }
@@ -848,13 +1008,6 @@ int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, 
   return coop_launch((const void *)apply_kernel, grid, smem, st, args);
 }
 
-int launch_setup_tables(const Args &A, int grid, size_t smem, cudaStream_t st, const SetupArgs &T) {
-  Args a = A;
-  SetupArgs t = T;
-  void *args[] = {&a, &t};
-  return coop_launch((const void *)setup_kernel, grid, smem, st, args);
-}
-
 int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const double *omega,
                  double2 *What, double2 *LamW, double2 *LamQ, double2 *BhI, double2 *BhF,
                  double2 *chirpI, double2 *twL, double beta, int precond) {
@@ -869,11 +1022,15 @@ int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const do
   T.chirpI = chirpI;
   T.twL = twL;
   T.precond = precond;
-  return launch_setup_tables(A, grid, smem, st, T);
+  Args a = A;
+  void *args[] = {&a, &T};
+  return coop_launch((const void *)setup_kernel, grid, smem, st, args);
 }
 
 int launch_weights(double *omega, double *g_tmp, int n, double beta, cudaStream_t st) {
-  grunwald_kernel<<<1, 32, 0, st>>>(g_tmp, n + 1, beta);
+  // factors in omega's storage first, then the sequential product into g_tmp, then omega
+  grunwald_factors_kernel<<<(n + 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(omega, n + 1, beta);
+  grunwald_kernel<<<1, 32, 0, st>>>(g_tmp, omega, n + 1);
   wsgd_kernel<<<(n + 2 + kThreads - 1) / kThreads, kThreads, 0, st>>>(g_tmp, omega, n + 1, beta);
   return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
 }
@@ -885,8 +1042,6 @@ int launch_time_tables(int M, double alpha, double tau, double h, double beta, c
       M, alpha, tau, h, beta, gam, dp, dm, hc, hl, eta, q, kp, km);
   return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
 }
-
-
 
 // ================================================================================================
 // Operator product without any device allocation.
@@ -966,7 +1121,7 @@ static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, do
   }
   if (!grid_sync(A)) return;
   // spectrum of W's circulant embedding (t_0 = omega_1, ..., t_{n-1} = omega_n, t_{-1} = omega_0)
-  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
                         [&](int m, double2) -> double2 {
                           double v[2];
 #pragma unroll
@@ -977,7 +1132,7 @@ static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, do
                           return make_double2(v[0], v[1]);
                         });
   if (!grid_sync(A)) return;
-  row_pass<1>(A, S, nullptr, const_cast<double2 *>(A.What), 1.0, -1);
+  row_pass<1, double2>(A, S, A.twL, A.Y1, nullptr, nullptr, const_cast<double2 *>(A.What), 1.0, -1);
   if (!grid_sync(A)) return;
   // operator spectrum: A = eta I - sigma L or B = eta I + (1-sigma) L, scaled 1/(4N)
   {
@@ -995,12 +1150,12 @@ static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, do
     }
   }
   if (!grid_sync(A)) return;
-  col_pass<false, true>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
                         [&](int m, double2) -> double2 { return ld2(xin, m); });
   if (!grid_sync(A)) return;
-  row_pass<0>(A, S, A.SA, nullptr, 0.0, -1);
+  row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, A.SA, nullptr, 0.0, -1);
   if (!grid_sync(A)) return;
-  col_pass<true, false>(A, S, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
+  col_pass<true, false, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, nullptr,
                         [&](int m, double2 z) -> double2 {
                           if (2 * m < n) y[2 * m] = z.x;
                           if (2 * m + 1 < n) y[2 * m + 1] = z.y;

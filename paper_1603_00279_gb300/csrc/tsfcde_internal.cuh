@@ -26,6 +26,7 @@ constexpr long long kSpinLimit = 1ll << 23;   // bound on a barrier wait (about 
 // status codes (mirror include/tsfcde.h)
 constexpr int kOK = 0, kEInvalid = 1, kENoMem = 2, kECuda = 3, kENonFinite = 4,
               kENotConverged = 5, kEBreakdown = 6, kESingular = 7, kETimeout = 8, kEState = 9;
+constexpr int kFP64 = 0, kMixed = 1;
 
 struct ConvPlan {  // real length L, complex length N = L/2 = N1 * N2
   int L, lgL, N, lgN, N1, lg1, N2, lg2;
@@ -71,10 +72,21 @@ struct Args {
   int *status;            // [0] status, [1] abort flag
   int *iters;             // M
   double *resid;          // M
+  // mixed precision (FP32 inner CGS inside FP64 iterative refinement)
+  int precision;          // 0 FP64, 1 mixed
+  double inner_tol;       // relative residual target of each FP32 inner solve
+  int inner_maxit, outer_maxit;
+  double *g;              // FP64 right-hand side of the level
+  float *x32, *r32, *rt32, *p32, *q32, *uu32, *vh32;   // FP32 inner Krylov vectors (L each)
+  float2 *SA32, *SP32;    // FP32 copies of the level spectra (rounded from FP64)
+  float2 *Y1f, *Y2f;      // FP32 FFT work, L/2 complex each
+  float2 *twL32;          // FP32 twiddles (rounded from the FP64 table)
+  int *outer_iters;       // M: refinement steps per level
+  int *escalated;         // M: 1 if the level fell back to FP64 CGS
 };
 
 // ---------------------------------------------------------------------------------------------
-// complex helpers
+// complex helpers (double2 for the FP64 path, float2 for the FP32 inner solve)
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -89,6 +101,25 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 __device__ __forceinline__ double2 mul_i(double2 a) { return make_double2(-a.y, a.x); }     // * i
 __device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }    // * -i
 
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+template <typename T> struct RealOf;
+template <> struct RealOf<double2> { using R = double; };
+template <> struct RealOf<float2> { using R = float; };
+__device__ __forceinline__ void mkc(double2 &z, double x, double y) { z = make_double2(x, y); }
+__device__ __forceinline__ void mkc(float2 &z, float x, float y) { z = make_float2(x, y); }
+
 // ---------------------------------------------------------------------------------------------
 // Stockham radix-4/2 FFT of `nl` lines of length P = 2^lgP in shared memory.
 // Line l occupies a[l*P .. l*P+P); b is a scratch area of the same size.  SIGN = -1 forward,
@@ -99,9 +130,8 @@ __device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, 
 // is twiddled by e^{SIGN 2 pi i q k/(r Ls)}, an r-point DFT is taken, and output q goes to
 // y[(j - k) r + k + q Ls].
 // ---------------------------------------------------------------------------------------------
-template <int SIGN>
-__device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, int nl,
-                                             const double2 *tw, int lgT) {
+template <int SIGN, typename T>
+__device__ __forceinline__ T *smem_fft(T *a, T *b, int lgP, int nl, const T *tw, int lgT) {
   const int P = 1 << lgP;
   int lgLs = 0;
   while (lgLs < lgP) {
@@ -114,20 +144,20 @@ __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, in
         const int l = t >> (lgP - 2);
         const int j = t & (Q - 1);
         const int k = j & (Ls - 1);
-        const double2 *x = a + l * P;
-        double2 *y = b + l * P;
-        double2 a0 = x[j], a1 = x[j + Q], a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
+        const T *x = a + l * P;
+        T *y = b + l * P;
+        T a0 = x[j], a1 = x[j + Q], a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
         if (k) {
-          double2 w1 = tw[k << sh];
-          double2 w2 = tw[(2 * k) << sh];
-          double2 w3 = tw[(3 * k) << sh];
+          T w1 = tw[k << sh];
+          T w2 = tw[(2 * k) << sh];
+          T w3 = tw[(3 * k) << sh];
           if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
           a1 = cmul(a1, w1);
           a2 = cmul(a2, w2);
           a3 = cmul(a3, w3);
         }
-        const double2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
-        const double2 b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
+        const T b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+        const T b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
         const int base = ((j - k) << 2) + k;
         y[base] = cadd(b0, b2);
         y[base + Ls] = cadd(b1, b3);
@@ -143,11 +173,11 @@ __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, in
         const int l = t >> (lgP - 1);
         const int j = t & (Q - 1);
         const int k = j & (Ls - 1);
-        const double2 *x = a + l * P;
-        double2 *y = b + l * P;
-        double2 a0 = x[j], a1 = x[j + Q];
+        const T *x = a + l * P;
+        T *y = b + l * P;
+        T a0 = x[j], a1 = x[j + Q];
         if (k) {
-          double2 w1 = tw[k << sh];
+          T w1 = tw[k << sh];
           if (SIGN > 0) w1 = cconj(w1);
           a1 = cmul(a1, w1);
         }
@@ -158,7 +188,7 @@ __device__ __forceinline__ double2 *smem_fft(double2 *a, double2 *b, int lgP, in
       lgLs += 1;
     }
     __syncthreads();
-    double2 *t = a;
+    T *t = a;
     a = b;
     b = t;
   }

@@ -1,0 +1,59 @@
+"""Mixed precision (FP32 inner CGS inside FP64 iterative refinement) against the FP64 oracle and
+the FP64 GPU path: relative L2 gap <= 1e-8 per level."""
+import numpy as np
+import pytest
+
+import oracle as O
+import tsfcde_workloads as W
+from gpu_common import rel_l2, solver_module
+
+pytestmark = pytest.mark.gpu
+
+
+def _levels(P, prob, nlev, **kw):
+    s = P.Solver.from_problem(prob, source="separable", **kw)
+    out = [s.get_level()[0]]
+    stats = []
+    for _ in range(nlev):
+        stats.append(s.step(1))
+        out.append(s.get_level()[0])
+    s.close()
+    return out, stats
+
+
+@pytest.mark.parametrize("precond", ["strang", "tchan"])
+def test_mixed_small_config_every_level(precond):
+    P = solver_module()
+    prob = W.config_small(preconditioner=precond)
+    ref = O.run(prob)
+    got, st = _levels(P, prob, prob.M, precision="mixed")
+    assert max(rel_l2(got[j], ref[j]) for j in range(prob.M + 1)) <= 1e-8
+    assert sum(s["outer_iterations"] for s in st) >= prob.M
+
+
+def test_mixed_parameters_of_the_precision_workload():
+    """alpha = 0.8, beta = 1.5, gamma = 1, d+- = (1 +- t/2)/2 at n = 1023: first 8 levels."""
+    P = solver_module()
+    prob = W.config_mixed(n=1023, M=512)
+    ref = O.run(prob, levels=8)
+    got, st = _levels(P, prob, 8, precision="mixed")
+    assert max(rel_l2(got[j], ref[j]) for j in range(9)) <= 1e-8
+    assert sum(s["escalated_levels"] for s in st) == 0
+
+
+def test_mixed_matches_fp64_gpu_path():
+    P = solver_module()
+    prob = W.config_mixed(n=4095, M=64)
+    a, _ = _levels(P, prob, 16, precision="fp64")
+    b, st = _levels(P, prob, 16, precision="mixed")
+    assert max(rel_l2(b[j], a[j]) for j in range(17)) <= 1e-8
+
+
+def test_mixed_escalates_when_fp32_cannot_converge():
+    """beta = 1.9, alpha = 0.3 at n = 4095: u32 * kappa_eff ~ 0.3, the FP32 inner solve cannot
+    make progress; such levels must be finished by the FP64 CGS and still match FP64."""
+    P = solver_module()
+    prob = W.config_large(n=4095, M=1024, preconditioner="strang")
+    a, _ = _levels(P, prob, 6, precision="fp64")
+    b, st = _levels(P, prob, 6, precision="mixed")
+    assert max(rel_l2(b[j], a[j]) for j in range(7)) <= 1e-8
