@@ -180,6 +180,36 @@ int tsfcde_apply_operator_static(int64_t N, double beta, double sigma, double et
                                  double kappa_plus, double kappa_minus, int32_t op,
                                  const double *x, double *y, void *stream);
 
+/* ---- batched instances ----------------------------------------------------------------------
+ * Many independent TSFCDE instances with their own N, alpha, beta and constant coefficients,
+ * advanced together: each device CTA takes whole instances from a work queue (largest first)
+ * and runs their level solves with CTA-local barriers only.  All instances share M and the
+ * options (preconditioner, tol, maxit, precision).  f = 0 for batched instances. */
+typedef struct tsfcde_instance {
+  double a, b, T;         /* domain [a,b], final time T                                     */
+  int64_t N;              /* interior points, 1 <= N <= 16383                               */
+  double alpha, beta;     /* orders, as in tsfcde_setup                                      */
+  double gamma, d_plus, d_minus;   /* constant coefficients (d_plus, d_minus >= 0)          */
+  const double *u0;       /* N host values of u^0 (copied during setup)                     */
+} tsfcde_instance;
+
+typedef struct tsfcde_batch tsfcde_batch;
+
+/* Set up `count` instances with M levels each.  Device memory: per instance its state, history
+ * of increments (M x N FP64) and spectra; per CTA the work arrays of the largest instance. */
+int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance *inst, int64_t M,
+                       const tsfcde_options *opt);
+/* Advance every instance by nsteps levels (one device launch).  stats sums over instances. */
+int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats);
+/* Copy instance i's current level (N_i host values); *level receives j. */
+int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, double *u_out, int64_t *level);
+/* Per-level CGS iterations and final residuals of instance i, levels 0..count-1. */
+int tsfcde_batch_get_history(tsfcde_batch *b, int64_t i, int32_t *iters, double *resid, int64_t count);
+/* Every instance back to level 0 with its u^0 (device copy, no host transfer). */
+int tsfcde_batch_reset(tsfcde_batch *b);
+/* Release everything.  NULL is allowed. */
+void tsfcde_batch_free(tsfcde_batch *b);
+
 /* Release everything the context holds.  NULL is allowed. */
 void tsfcde_free(tsfcde_ctx *ctx);
 

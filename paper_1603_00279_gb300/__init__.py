@@ -55,6 +55,12 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Instance(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("T", C.c_double), ("N", C.c_int64),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("d_plus", C.c_double), ("d_minus", C.c_double), ("u0", C.POINTER(C.c_double))]
+
+
 class TsfcdeError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({status})")
@@ -94,6 +100,18 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_apply.restype = C.c_int
     lib.tsfcde_apply_operator_static.argtypes = [i64, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, vp, vp]
     lib.tsfcde_apply_operator_static.restype = C.c_int
+    lib.tsfcde_batch_setup.argtypes = [C.POINTER(vp), i64, C.POINTER(Instance), i64, C.POINTER(Options)]
+    lib.tsfcde_batch_setup.restype = C.c_int
+    lib.tsfcde_batch_step.argtypes = [vp, i64, C.POINTER(Stats)]
+    lib.tsfcde_batch_step.restype = C.c_int
+    lib.tsfcde_batch_get_level.argtypes = [vp, i64, pd, C.POINTER(i64)]
+    lib.tsfcde_batch_get_level.restype = C.c_int
+    lib.tsfcde_batch_get_history.argtypes = [vp, i64, C.POINTER(i32), pd, i64]
+    lib.tsfcde_batch_get_history.restype = C.c_int
+    lib.tsfcde_batch_reset.argtypes = [vp]
+    lib.tsfcde_batch_reset.restype = C.c_int
+    lib.tsfcde_batch_free.argtypes = [vp]
+    lib.tsfcde_batch_free.restype = None
     lib.tsfcde_free.argtypes = [vp]
     lib.tsfcde_free.restype = None
     lib.tsfcde_strerror.argtypes = [C.c_int]
@@ -246,6 +264,79 @@ class Solver:
         if getattr(self, "ctx", None):
             self.lib.tsfcde_free(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Independent constant-coefficient instances advanced together (tsfcde_batch_*).
+
+    problems: objects with a, b, T, n, alpha, beta, gamma(t), d_plus(t), d_minus(t), phi(x)
+    (coefficients are sampled once, at t = 0, since batched instances take constants); all
+    share M."""
+
+    def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
+                 maxit: int = 2000, precision: str = "fp64", device: int = 0,
+                 stream: Optional[int] = None):
+        self.lib = load_library()
+        self.M = int(M)
+        self.n = [int(p.n) for p in problems]
+        self._u0 = []
+        arr = (Instance * len(problems))()
+        for k, p in enumerate(problems):
+            x = p.a + (p.b - p.a) / (p.n + 1) * np.arange(1, p.n + 1, dtype=np.float64)
+            u0 = np.ascontiguousarray(p.phi(x), dtype=np.float64)
+            self._u0.append(u0)
+            arr[k] = Instance(p.a, p.b, p.T, p.n, p.alpha, p.beta, float(p.gamma(0.0)),
+                              float(p.d_plus(0.0)), float(p.d_minus(0.0)), _dptr(u0))
+        opt = Options()
+        self.lib.tsfcde_default_options(C.byref(opt))
+        opt.preconditioner = PRECONDITIONERS[preconditioner]
+        opt.tol = tol
+        opt.maxit = maxit
+        opt.precision = PRECISIONS[precision]
+        opt.device = device
+        opt.stream = stream
+        h = C.c_void_p()
+        _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
+               "tsfcde_batch_setup")
+        self.h = h
+
+    def step(self, nsteps: int = 1) -> dict:
+        s = Stats()
+        _check(self.lib.tsfcde_batch_step(self.h, nsteps, C.byref(s)), "tsfcde_batch_step", True)
+        return s.as_dict()
+
+    def get_level(self, i: int):
+        out = np.empty(self.n[i])
+        j = C.c_int64()
+        _check(self.lib.tsfcde_batch_get_level(self.h, i, _dptr(out), C.byref(j)), "tsfcde_batch_get_level")
+        return out, j.value
+
+    def history(self, i: int, count: int):
+        it = np.zeros(count, dtype=np.int32)
+        rs = np.zeros(count)
+        _check(self.lib.tsfcde_batch_get_history(self.h, i, it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 _dptr(rs), count), "tsfcde_batch_get_history")
+        return it, rs
+
+    def reset(self):
+        _check(self.lib.tsfcde_batch_reset(self.h), "tsfcde_batch_reset")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsfcde_batch_free(self.h)
+            self.h = None
 
     def __del__(self):
         try:

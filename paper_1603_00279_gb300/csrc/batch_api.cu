@@ -1,0 +1,448 @@
+// Host side of the batched C ABI (include/tsfcde.h, "batched instances"): per-instance tables
+// and state, per-CTA work arrays sized for the largest instance, the work-queue order, and the
+// launches of batch_setup_kernel / batch_level_kernel (level_kernels.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/tsfcde.h"
+#include "tsfcde_internal.cuh"
+
+using tsf::Args;
+
+struct tsfcde_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = true;
+  int64_t count = 0, M = 0, level = 0;
+  tsfcde_options opt;
+  std::vector<Args> inst;            // host copies (device pointers inside)
+  std::vector<int64_t> n;
+  std::vector<size_t> u0_off;
+  char *arena = nullptr, *scratch = nullptr;
+  Args *d_inst = nullptr;
+  tsf::InstanceSetup *d_setup = nullptr;
+  tsf::CtaScratch *d_cta = nullptr;
+  int *d_order = nullptr;
+  unsigned *d_next = nullptr;
+  double *d_u0 = nullptr;            // all instances' u^0, concatenated (L_i doubles each)
+  int grid = 0;
+  size_t smem = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TSFCDE_OK;
+  if (e == cudaErrorMemoryAllocation) return TSFCDE_E_NOMEM;
+  return TSFCDE_E_CUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+struct Carver {
+  size_t off = 0;
+  char *base = nullptr;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+void plan(Args &A, int64_t n) {
+  const int lgL = std::max(3, ilog2(2 * n));
+  A.cp.lgL = lgL;
+  A.cp.L = 1 << lgL;
+  A.cp.lgN = lgL - 1;
+  A.cp.N = 1 << A.cp.lgN;
+  A.cp.lg1 = A.cp.lgN / 2;
+  A.cp.lg2 = A.cp.lgN - A.cp.lg1;
+  A.cp.N1 = 1 << A.cp.lg1;
+  A.cp.N2 = 1 << A.cp.lg2;
+  A.bp.lgNc = lgL;
+  A.bp.Nc = 1 << lgL;
+  A.bp.lg1 = lgL / 2;
+  A.bp.lg2 = lgL - A.bp.lg1;
+  A.bp.N1 = 1 << A.bp.lg1;
+  A.bp.N2 = 1 << A.bp.lg2;
+  // one-CTA team: every item of a pass belongs to the CTA, processed in chunks
+  const int budget = 2048;
+  auto cap = [&](int items, int lines_per_item, int lg) {
+    return std::max(1, std::min(items, std::max(1, (budget >> lg) / lines_per_item)));
+  };
+  A.cap_col = cap(A.cp.N2, 1, A.cp.lg1);
+  A.cap_row = cap(A.cp.N1 / 2 + 1, 2, A.cp.lg2);
+  A.cap_bcol = cap(A.bp.N2, 1, A.bp.lg1);
+  A.cap_brow = cap(A.bp.N1, 1, A.bp.lg2);
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsfcde_batch_free(tsfcde_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->arena) cudaFree(b->arena);
+  if (b->scratch) cudaFree(b->scratch);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->stream && b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
+  const int64_t K = b->count, M = b->M;
+  const bool mixed = b->opt.precision == TSFCDE_MIXED;
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, b->device));
+  b->grid = 2 * prop.multiProcessorCount;
+  // ---- per-instance plans and the largest sizes ----
+  b->inst.assign(K, Args());
+  b->n.resize(K);
+  int lgLmax = 3;
+  int64_t nmax = 1;
+  size_t smax = 0;
+  for (int64_t i = 0; i < K; ++i) {
+    Args &A = b->inst[i];
+    std::memset(&A, 0, sizeof(A));
+    A.n = (int)in[i].N;
+    A.M = (int)M;
+    plan(A, in[i].N);
+    A.precond = b->opt.preconditioner;
+    A.sigma = 1.0 - in[i].alpha / 2.0;
+    const double tau = in[i].T / (double)M;
+    A.hscale = std::pow(tau, -in[i].alpha) / std::tgamma(2.0 - in[i].alpha);
+    A.tol = b->opt.tol;
+    A.maxit = b->opt.maxit;
+    A.precision = b->opt.precision;
+    A.inner_tol = b->opt.inner_tol;
+    A.inner_maxit = b->opt.inner_maxit;
+    A.outer_maxit = b->opt.outer_maxit;
+    b->n[i] = in[i].N;
+    lgLmax = std::max(lgLmax, A.cp.lgL);
+    nmax = std::max(nmax, in[i].N);
+    smax = std::max(smax, tsf::level_smem_bytes(A));
+  }
+  b->smem = smax;
+  if (b->smem > prop.sharedMemPerBlockOptin) return TSFCDE_E_INVALID_ARG;
+  for (const void *fn : {tsf::batch_level_kernel_ptr(), tsf::batch_setup_kernel_ptr()}) {
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, b->smem));
+    if (occ < 1) return TSFCDE_E_INVALID_ARG;
+    b->grid = std::min(b->grid, occ * prop.multiProcessorCount);
+  }
+  const size_t Lmax = size_t(1) << lgLmax, Nmax = Lmax / 2;
+
+  // ---- per-instance arena ----
+  std::vector<tsf::InstanceSetup> setup(K);
+  Carver cv;
+  size_t u0_total = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    cv.off = 0;
+    cv.base = pass ? b->arena : nullptr;
+    for (int64_t i = 0; i < K; ++i) {
+      Args &A = b->inst[i];
+      const size_t L = A.cp.L, N = A.cp.N, n = A.n;
+      A.u = cv.take<double>(L);
+      A.ring_stride = (long long)((n + 31) / 32 * 32);
+      A.ring = cv.take<double>((size_t)M * A.ring_stride);
+      A.twL = cv.take<double2>(L);
+      A.What = cv.take<double2>(N + 1);
+      A.LamW = cv.take<double2>(n);
+      A.LamQ = cv.take<double2>(n);
+      A.chirpI = cv.take<double2>(n);
+      A.BhI = cv.take<double2>(L);
+      setup[i].BhF = cv.take<double2>(L);
+      setup[i].omega = cv.take<double>(n + 2);
+      setup[i].gtmp = cv.take<double>(n + 2);
+      A.lv_eta = cv.take<double>(M);
+      A.lv_q = cv.take<double>(M);
+      A.lv_kp = cv.take<double>(M);
+      A.lv_km = cv.take<double>(M);
+      A.lv_newsym = cv.take<int>(M);
+      A.hc = cv.take<double>(M + 2);
+      A.hl = cv.take<double>(M + 2);
+      A.iters = cv.take<int>(M);
+      A.resid = cv.take<double>(M);
+      A.outer_iters = cv.take<int>(M);
+      A.escalated = cv.take<int>(M);
+      A.status = cv.take<int>(4);
+      if (mixed) A.twL32 = cv.take<float2>(L);
+    }
+    b->u0_off.assign(K, 0);
+    double *u0base = cv.take<double>(1);
+    (void)u0base;
+    u0_total = 0;
+    for (int64_t i = 0; i < K; ++i) {
+      b->u0_off[i] = u0_total;
+      u0_total += (size_t)b->n[i];
+    }
+    b->d_u0 = cv.take<double>(u0_total);
+    if (!pass) {
+      CK(cudaMalloc(&b->arena, cv.off + 256));
+      CK(cudaMemsetAsync(b->arena, 0, cv.off + 256, b->stream));
+    }
+  }
+  // ---- per-CTA scratch ----
+  std::vector<tsf::CtaScratch> cta(b->grid);
+  Carver cs;
+  for (int pass = 0; pass < 2; ++pass) {
+    cs.off = 0;
+    cs.base = pass ? b->scratch : nullptr;
+    for (int c = 0; c < b->grid; ++c) {
+      tsf::CtaScratch &C = cta[c];
+      C.x = cs.take<double>(Lmax);
+      C.r = cs.take<double>(Lmax);
+      C.rt = cs.take<double>(Lmax);
+      C.p = cs.take<double>(Lmax);
+      C.q = cs.take<double>(Lmax);
+      C.uu = cs.take<double>(Lmax);
+      C.vh = cs.take<double>(Lmax);
+      C.H = cs.take<double>(Lmax);
+      C.cprime = cs.take<double>(nmax);
+      C.partials = cs.take<double>(8);
+      C.bar = cs.take<unsigned>(tsf::kBarWords);
+      C.SA = cs.take<double2>(Nmax + 1);
+      C.SB = cs.take<double2>(Nmax + 1);
+      C.SP = cs.take<double2>(Nmax + 1);
+      C.Y1 = cs.take<double2>(Lmax);
+      C.Y2 = cs.take<double2>(Lmax);
+      if (mixed) {
+        C.g = cs.take<double>(Lmax);
+        C.x32 = cs.take<float>(Lmax);
+        C.r32 = cs.take<float>(Lmax);
+        C.rt32 = cs.take<float>(Lmax);
+        C.p32 = cs.take<float>(Lmax);
+        C.q32 = cs.take<float>(Lmax);
+        C.uu32 = cs.take<float>(Lmax);
+        C.vh32 = cs.take<float>(Lmax);
+        C.SA32 = cs.take<float2>(Nmax + 1);
+        C.SP32 = cs.take<float2>(Nmax + 1);
+        C.Y1f = cs.take<float2>(Nmax);
+        C.Y2f = cs.take<float2>(Nmax);
+      }
+    }
+    if (!pass) {
+      CK(cudaMalloc(&b->scratch, cs.off + 256));
+      CK(cudaMemsetAsync(b->scratch, 0, cs.off + 256, b->stream));
+    }
+  }
+  // ---- setup inputs, order (largest first), uploads ----
+  std::vector<double> u0all(u0_total);
+  for (int64_t i = 0; i < K; ++i) {
+    const tsfcde_instance &I = in[i];
+    tsf::InstanceSetup &S = setup[i];
+    S.alpha = I.alpha;
+    S.beta = I.beta;
+    S.tau = I.T / (double)M;
+    S.h = (I.b - I.a) / (double)(I.N + 1);
+    S.gamma = I.gamma;
+    S.d_plus = I.d_plus;
+    S.d_minus = I.d_minus;
+    std::memcpy(u0all.data() + b->u0_off[i], I.u0, (size_t)I.N * sizeof(double));
+  }
+  std::vector<int> order(K);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+  CK(cudaMalloc(&b->d_inst, K * sizeof(Args)));
+  CK(cudaMalloc(&b->d_setup, K * sizeof(tsf::InstanceSetup)));
+  CK(cudaMalloc(&b->d_cta, b->grid * sizeof(tsf::CtaScratch)));
+  CK(cudaMalloc(&b->d_order, K * sizeof(int)));
+  CK(cudaMalloc(&b->d_next, 256));
+  CK(cudaMemcpyAsync(b->d_inst, b->inst.data(), K * sizeof(Args), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_setup, setup.data(), K * sizeof(tsf::InstanceSetup), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_cta, cta.data(), b->grid * sizeof(tsf::CtaScratch), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_order, order.data(), K * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_u0, u0all.data(), u0_total * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  // ---- device setup: weights, tables, spectra of every instance ----
+  tsf::BatchArgs B;
+  B.count = (int)K;
+  B.inst = b->d_inst;
+  B.setup = b->d_setup;
+  B.cta = b->d_cta;
+  B.order = b->d_order;
+  B.next = b->d_next;
+  CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
+  int st = tsf::launch_batch(B, b->grid, b->smem, b->stream, 1, 0, 0);
+  if (st) return st;
+  CK(cudaStreamSynchronize(b->stream));
+  for (int64_t i = 0; i < K; ++i) {
+    int h[2];
+    CK(cudaMemcpy(h, b->inst[i].status, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0]) return h[0];
+  }
+  return tsfcde_batch_reset(b);
+}
+
+int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance *inst, int64_t M,
+                       const tsfcde_options *opt) {
+  if (!out) return TSFCDE_E_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !inst || M < 1 || M > (int64_t(1) << 30)) return TSFCDE_E_INVALID_ARG;
+  tsfcde_options o;
+  tsfcde_default_options(&o);
+  if (opt) o = *opt;
+  if (o.preconditioner < 0 || o.preconditioner > 2 ||
+      (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1)
+    return TSFCDE_E_INVALID_ARG;
+  for (int64_t i = 0; i < count; ++i) {
+    const tsfcde_instance &I = inst[i];
+    if (!(I.a < I.b) || !(I.T > 0) || I.N < 1 || I.N > 16383 || !(I.alpha > 0 && I.alpha <= 1) ||
+        !(I.beta > 1 && I.beta <= 2) || !(I.d_plus >= 0) || !(I.d_minus >= 0) || !I.u0 ||
+        !std::isfinite(I.gamma))
+      return TSFCDE_E_INVALID_ARG;
+    for (int64_t k = 0; k < I.N; ++k)
+      if (!std::isfinite(I.u0[k])) return TSFCDE_E_NONFINITE;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
+  tsfcde_batch *b = new tsfcde_batch();
+  b->device = o.device;
+  b->opt = o;
+  b->count = count;
+  b->M = M;
+  if (cudaSetDevice(b->device) != cudaSuccess) {
+    delete b;
+    return TSFCDE_E_CUDA;
+  }
+  if (o.stream) {
+    b->stream = (cudaStream_t)o.stream;
+    b->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return TSFCDE_E_CUDA;
+  }
+  if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    tsfcde_batch_free(b);
+    return TSFCDE_E_CUDA;
+  }
+  const int st = batch_setup_impl(b, inst);
+  if (st != TSFCDE_OK) {
+    tsfcde_batch_free(b);
+    return st;
+  }
+  *out = b;
+  return TSFCDE_OK;
+}
+
+int tsfcde_batch_reset(tsfcde_batch *b) {
+  if (!b) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(b->device));
+  for (int64_t i = 0; i < b->count; ++i)
+    CK(cudaMemcpyAsync(b->inst[i].u, b->d_u0 + b->u0_off[i], b->n[i] * sizeof(double),
+                       cudaMemcpyDeviceToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  b->level = 0;
+  return TSFCDE_OK;
+}
+
+int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
+  if (!b || nsteps < 0) return TSFCDE_E_INVALID_ARG;
+  if (b->level + nsteps > b->M) return TSFCDE_E_STATE;
+  CK(cudaSetDevice(b->device));
+  const int64_t j0 = b->level, j1 = b->level + nsteps;
+  float ms = 0.f;
+  int launches = 0;
+  if (nsteps > 0) {
+    for (int64_t i = 0; i < b->count; ++i) CK(cudaMemsetAsync(b->inst[i].status, 0, 4 * sizeof(int), b->stream));
+    CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
+    tsf::BatchArgs B;
+    B.count = (int)b->count;
+    B.inst = b->d_inst;
+    B.setup = b->d_setup;
+    B.cta = b->d_cta;
+    B.order = b->d_order;
+    B.next = b->d_next;
+    CK(cudaEventRecord(b->ev0, b->stream));
+    const int st = tsf::launch_batch(B, b->grid, b->smem, b->stream, 0, (int)j0, (int)j1);
+    if (st) return st;
+    CK(cudaEventRecord(b->ev1, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    launches = 1;
+  }
+  int worst = TSFCDE_OK;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->min_iterations = 1 << 30;
+  }
+  for (int64_t i = 0; i < b->count && nsteps > 0; ++i) {
+    int h[2];
+    CK(cudaMemcpy(h, b->inst[i].status, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0] && h[0] != TSFCDE_E_NOT_CONVERGED) return h[0];
+    if (h[0]) worst = h[0];
+    if (stats) {
+      std::vector<int> it(nsteps), oi(nsteps), es(nsteps);
+      std::vector<double> rs(nsteps);
+      CK(cudaMemcpy(it.data(), b->inst[i].iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(rs.data(), b->inst[i].resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+      if (b->opt.precision == TSFCDE_MIXED) {
+        CK(cudaMemcpy(oi.data(), b->inst[i].outer_iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(es.data(), b->inst[i].escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+      }
+      for (int64_t k = 0; k < nsteps; ++k) {
+        stats->total_iterations += it[k];
+        stats->max_iterations = std::max(stats->max_iterations, it[k]);
+        stats->min_iterations = std::min(stats->min_iterations, it[k]);
+        stats->max_residual = std::max(stats->max_residual, rs[k]);
+        if (b->opt.precision == TSFCDE_MIXED) {
+          stats->outer_iterations += oi[k];
+          stats->escalated_levels += es[k];
+        }
+      }
+    }
+  }
+  b->level = j1;
+  if (stats) {
+    stats->level = b->level;
+    stats->levels_advanced = nsteps;
+    stats->status = worst;
+    stats->device_launches = launches;
+    stats->device_ms = ms;
+    if (stats->min_iterations == (1 << 30)) stats->min_iterations = 0;
+  }
+  return worst;
+}
+
+int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, double *u_out, int64_t *level) {
+  if (!b || i < 0 || i >= b->count) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(b->device));
+  if (level) *level = b->level;
+  if (u_out) {
+    CK(cudaMemcpyAsync(u_out, b->inst[i].u, b->n[i] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  return TSFCDE_OK;
+}
+
+int tsfcde_batch_get_history(tsfcde_batch *b, int64_t i, int32_t *iters, double *resid, int64_t count) {
+  if (!b || i < 0 || i >= b->count || count < 0 || count > b->level) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(b->device));
+  if (count == 0) return TSFCDE_OK;
+  if (iters) CK(cudaMemcpy(iters, b->inst[i].iters, count * sizeof(int), cudaMemcpyDeviceToHost));
+  if (resid) CK(cudaMemcpy(resid, b->inst[i].resid, count * sizeof(double), cudaMemcpyDeviceToHost));
+  return TSFCDE_OK;
+}
+
+}  // extern "C"

@@ -64,10 +64,14 @@ __device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S,
 
 // Contiguous item range of this CTA: [lo, hi).
 __device__ __forceinline__ void my_items(int nitems, int &lo, int &hi) {
-  const int per = (nitems + gridDim.x - 1) / gridDim.x;
-  lo = min(nitems, blockIdx.x * per);
+  const TeamInfo t = team();
+  const int per = (nitems + t.cnt - 1) / t.cnt;
+  lo = min(nitems, t.idx * per);
   hi = min(nitems, lo + per);
 }
+// Grid-stride loop bounds over the team: first index and stride.
+__device__ __forceinline__ int team_tid() { return team().idx * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int team_threads() { return team().cnt * blockDim.x; }
 
 // ------------------------------------------------------------------------------------------------
 // Column pass of a four-step FFT: lines of P1 = 2^lg1 points, 2^lg2 of them, element m = m1*P2+m2.
@@ -128,6 +132,8 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *
 struct LevelScalars {
   double eta, q, kp, km;
 };
+__device__ __forceinline__ double l21_a(double alpha, double sigma, int l);
+__device__ __forceinline__ double l21_b(double alpha, double sigma, int l);
 
 __device__ __forceinline__ LevelScalars level_scalars(const Args &A, int j) {
   LevelScalars s;
@@ -311,7 +317,7 @@ __device__ __forceinline__ double2 lambda_p(const Args &A, const LevelScalars &s
 __device__ __forceinline__ void write_partials(const Args &A, const Smem &S, int rb, double (&acc)[3]) {
   block_sum<3>(acc, S.red);
   if (threadIdx.x == 0) {
-    double *p = A.partials + ((size_t)rb * gridDim.x + blockIdx.x) * 4;
+    double *p = A.partials + ((size_t)rb * team().cnt + team().idx) * 4;
     p[0] = acc[0];
     p[1] = acc[1];
     p[2] = acc[2];
@@ -321,8 +327,9 @@ __device__ __forceinline__ void write_partials(const Args &A, const Smem &S, int
 // Sum of all CTAs' partials of buffer rb, identical in every CTA (fixed order).
 __device__ __forceinline__ void read_partials(const Args &A, const Smem &S, int rb, double (&tot)[3]) {
   double v[3] = {0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double *p = A.partials + ((size_t)rb * gridDim.x + b) * 4;
+  const int cnt = team().cnt;
+  for (int b = threadIdx.x; b < cnt; b += blockDim.x) {
+    const double *p = A.partials + ((size_t)rb * cnt + b) * 4;
     v[0] += p[0];
     v[1] += p[1];
     v[2] += p[2];
@@ -390,7 +397,7 @@ __device__ void ph_pinv_c2(const Args &A, const Smem &S, int j) {
 __device__ void ph_ab_only(const Args &A, const Smem &S, int j) {
   const LevelScalars s = level_scalars(A, j);
   const ConvPlan &P = A.cp;
-  for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl <= P.N; sl += gridDim.x * blockDim.x) {
+  for (int sl = team_tid(); sl <= P.N; sl += team_threads()) {
     const int k = sl == P.N ? P.N : ((sl & (P.N2 - 1)) * P.N1 + (sl >> P.lg2));
     store_ab(A, s, sl, k, sl == P.N);
   }
@@ -419,7 +426,7 @@ __device__ void ph_history(const Args &A, int j, bool commit) {
   const int npair = (A.n + 1) >> 1;
   const long long st = A.ring_stride;
   const double2 *ring2 = reinterpret_cast<const double2 *>(A.ring);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
+  for (int t = team_tid(); t < npair; t += team_threads()) {
     double2 dlast = make_double2(0.0, 0.0);
     if (commit) {
       const double2 xv = reinterpret_cast<const double2 *>(A.x)[t];
@@ -462,7 +469,7 @@ __device__ void ph_history(const Args &A, int j, bool commit) {
 // Final commit (end of a launch): d^j = x - u into the ring, u = x.
 __device__ void ph_commit(const Args &A, int j) {
   const int npair = (A.n + 1) >> 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
+  for (int t = team_tid(); t < npair; t += team_threads()) {
     const double2 xv = reinterpret_cast<const double2 *>(A.x)[t];
     const double2 uv = reinterpret_cast<const double2 *>(A.u)[t];
     reinterpret_cast<double2 *>(A.ring + (long long)j * A.ring_stride)[t] = make_double2(xv.x - uv.x, xv.y - uv.y);
@@ -627,9 +634,8 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
 // ------------------------------------------------------------------------------------------------
 // the level kernel
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int j1) {
-  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
-  grid_sync_init();
+// March levels [j0, j1) of one instance with the current team (whole grid or one CTA).
+__device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   const int n = A.n;
   const bool mixed = A.precision == kMixed;
   int rb = 0;
@@ -775,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
         prev = rel;
       }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (team().idx == 0 && threadIdx.x == 0) {
       A.iters[j] = its;
       A.resid[j] = rel;
       if (mixed) {
@@ -791,6 +797,12 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
   }
   if (!grid_sync(A)) return;
   ph_commit(A, j1 - 1);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int j1) {
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
+  march_body(A, S, j0, j1);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -836,11 +848,10 @@ __device__ __forceinline__ double circ_col(const double *omega, int which, int k
   return k <= n / 2 ? toe_entry(omega, which, k) : toe_entry(omega, which, k - n);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T) {
-  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
-  grid_sync_init();
+// Per-instance tables and spectra with the current team.
+__device__ void setup_body(const Args &A, const SetupArgs &T, const Smem &S) {
   const int n = A.n, L = A.cp.L;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int gt = team_tid(), gs = team_threads();
   // tables: twiddles e^{-2 pi i k/L} (and their FP32 copy), chirp e^{i pi (k^2 mod 2n)/n}
   for (int k = gt; k < L; k += gs) {
     double s, c;
@@ -902,6 +913,127 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
                                      return z;
                                    });
     if (!grid_sync(A)) return;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T) {
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  grid_sync_init();
+  setup_body(A, T, S);
+}
+
+// ------------------------------------------------------------------------------------------------
+// batched instances: each CTA takes whole instances from a work queue and runs them with a
+// one-CTA team (no grid barriers); per-instance data in Args, per-CTA work arrays patched in.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void patch_cta_scratch(Args &A, const CtaScratch &C) {
+  A.x = C.x; A.r = C.r; A.rt = C.rt; A.p = C.p; A.q = C.q; A.uu = C.uu; A.vh = C.vh; A.H = C.H;
+  A.SA = C.SA; A.SB = C.SB; A.SP = C.SP; A.Y1 = C.Y1; A.Y2 = C.Y2; A.cprime = C.cprime;
+  A.partials = C.partials; A.bar = C.bar;
+  A.g = C.g; A.x32 = C.x32; A.r32 = C.r32; A.rt32 = C.rt32; A.p32 = C.p32; A.q32 = C.q32;
+  A.uu32 = C.uu32; A.vh32 = C.vh32; A.SA32 = C.SA32; A.SP32 = C.SP32; A.Y1f = C.Y1f; A.Y2f = C.Y2f;
+}
+
+// One instance's weights (Lemma 2) and level tables (Lemma 1) with a one-CTA team; constant
+// coefficients gamma, d+, d- given in the instance's lv_q/lv_kp/lv_km slots as raw values.
+__device__ void instance_tables(const Args &A, double *omega, double *gtmp, double alpha,
+                                double beta, double tau, double h, double gam, double dp, double dm) {
+  const int n = A.n, M = A.M;
+  for (int k = 1 + threadIdx.x; k <= n + 1; k += blockDim.x)
+    omega[k] = __dadd_rn(1.0, -__ddiv_rn(beta + 1.0, (double)k));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gk = 1.0;
+    gtmp[0] = gk;
+    for (int k = 1; k <= n + 1; ++k) {
+      gk = __dmul_rn(omega[k], gk);
+      gtmp[k] = gk;
+    }
+  }
+  __syncthreads();
+  const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
+  const double lam0 = (4.0 - beta * beta) / 6.0;
+  const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) {
+    double w = __dmul_rn(lam1, gtmp[k]);
+    if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, gtmp[k - 1]));
+    if (k >= 2) w = __dadd_rn(w, __dmul_rn(lamm1, gtmp[k - 2]));
+    omega[k] = w;
+  }
+  const double sigma = 1.0 - alpha / 2.0;
+  const double denom = pow(tau, alpha) * tgamma(2.0 - alpha);
+  const double hb = pow(h, beta);
+  double *hc = const_cast<double *>(A.hc), *hl = const_cast<double *>(A.hl);
+  double *eta = const_cast<double *>(A.lv_eta), *q = const_cast<double *>(A.lv_q);
+  double *kp = const_cast<double *>(A.lv_kp), *km = const_cast<double *>(A.lv_km);
+  int *ns = const_cast<int *>(A.lv_newsym);
+  for (int l = threadIdx.x; l <= M; l += blockDim.x) {
+    const double al = l21_a(alpha, sigma, l), bl = l21_b(alpha, sigma, l);
+    hl[l] = al - bl;
+    hc[l] = l >= 1 ? al + l21_b(alpha, sigma, l + 1) - bl : 0.0;
+    if (l < M) {
+      const double c0 = l == 0 ? l21_a(alpha, sigma, 0) : l21_a(alpha, sigma, 0) + l21_b(alpha, sigma, 1);
+      eta[l] = c0 / denom;
+      q[l] = gam / (2.0 * h);
+      kp[l] = dp / hb;
+      km[l] = dm / hb;
+      ns[l] = l <= 1;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int next_instance(const BatchArgs &B) {
+  __shared__ int s_i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned k = atomicAdd(B.next, 1u);
+    s_i = k < (unsigned)B.count ? B.order[k] : -1;
+  }
+  __syncthreads();
+  return s_i;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batch_setup_kernel(BatchArgs B) {
+  __shared__ Args sA;
+  cta_team_init();
+  for (int i = next_instance(B); i >= 0; i = next_instance(B)) {
+    if (threadIdx.x == 0) {
+      sA = B.inst[i];
+      patch_cta_scratch(sA, B.cta[blockIdx.x]);
+      team().grid = 0;
+    }
+    __syncthreads();
+    const InstanceSetup &I = B.setup[i];
+    instance_tables(sA, I.omega, I.gtmp, I.alpha, I.beta, I.tau, I.h, I.gamma, I.d_plus, I.d_minus);
+    SetupArgs T;
+    T.omega = I.omega;
+    T.What = const_cast<double2 *>(sA.What);
+    T.LamW = const_cast<double2 *>(sA.LamW);
+    T.LamQ = const_cast<double2 *>(sA.LamQ);
+    T.BhI = const_cast<double2 *>(sA.BhI);
+    T.BhF = I.BhF;
+    T.chirpI = const_cast<double2 *>(sA.chirpI);
+    T.twL = const_cast<double2 *>(sA.twL);
+    T.precond = sA.precond;
+    const Smem S = smem_view(lp_max_of(sA), tw_max_of(sA));
+    setup_body(sA, T, S);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batch_level_kernel(BatchArgs B, int j0, int j1) {
+  __shared__ Args sA;
+  cta_team_init();
+  for (int i = next_instance(B); i >= 0; i = next_instance(B)) {
+    if (threadIdx.x == 0) {
+      sA = B.inst[i];
+      patch_cta_scratch(sA, B.cta[blockIdx.x]);
+    }
+    __syncthreads();
+    const Smem S = smem_view(lp_max_of(sA), tw_max_of(sA));
+    march_body(sA, S, j0, j1);
+    __syncthreads();
   }
 }
 
@@ -992,6 +1124,16 @@ size_t level_smem_bytes(const Args &A) {
 }
 
 const void *level_kernel_ptr() { return (const void *)level_kernel; }
+const void *batch_level_kernel_ptr() { return (const void *)batch_level_kernel; }
+const void *batch_setup_kernel_ptr() { return (const void *)batch_setup_kernel; }
+
+int launch_batch(const BatchArgs &B, int grid, size_t smem, cudaStream_t st, int setup, int j0, int j1) {
+  if (setup)
+    batch_setup_kernel<<<grid, kThreads, smem, st>>>(B);
+  else
+    batch_level_kernel<<<grid, kThreads, smem, st>>>(B, j0, j1);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+}
 const void *apply_kernel_ptr() { return (const void *)apply_kernel; }
 const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
 

@@ -219,14 +219,40 @@ __device__ __forceinline__ void raise_fatal(const Args &A, int code) {
 constexpr int kMaxGrid = 1024;
 constexpr int kBarWords = 32 + kMaxGrid;
 
+// The team of CTAs that works on one instance: the whole grid (one instance per launch) or a
+// single CTA (batched instances, one per CTA at a time).  Kept in shared memory, set at kernel
+// start; every work split, reduction and barrier of the level solve goes through it.
+struct TeamInfo {
+  int idx, cnt, grid;
+};
+__device__ __forceinline__ TeamInfo &team() {
+  __shared__ TeamInfo t;
+  return t;
+}
+
 // Per-CTA count of grid barriers passed in this launch.
 __device__ __forceinline__ unsigned long long &bar_count() {
   __shared__ unsigned long long k;
   return k;
 }
-// Run once at the start of every kernel that calls grid_sync.
+// Run once at the start of every kernel that calls grid_sync (the team is the whole grid).
 __device__ __forceinline__ void grid_sync_init() {
-  if (threadIdx.x == 0) bar_count() = 0ull;
+  if (threadIdx.x == 0) {
+    bar_count() = 0ull;
+    team().idx = blockIdx.x;
+    team().cnt = gridDim.x;
+    team().grid = 1;
+  }
+  __syncthreads();
+}
+// Team of one CTA (batched instances).
+__device__ __forceinline__ void cta_team_init() {
+  if (threadIdx.x == 0) {
+    bar_count() = 0ull;
+    team().idx = 0;
+    team().cnt = 1;
+    team().grid = 0;
+  }
   __syncthreads();
 }
 
@@ -248,6 +274,11 @@ __device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsig
 __device__ __forceinline__ bool grid_sync(const Args &A) {
   __shared__ int s_go;
   __syncthreads();
+  if (!team().grid) {   // one-CTA team: a block barrier orders the CTA's global writes
+    if (threadIdx.x == 0) s_go = ld_volatile_i32(A.status + 1) == 0;
+    __syncthreads();
+    return s_go != 0;
+  }
   if (threadIdx.x == 0) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(A.bar);
     const unsigned long long k = ++bar_count();
@@ -296,6 +327,29 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double *sm /* K*32 dou
   __syncthreads();
 }
 
+// Per-CTA work arrays of the batched solver (sized for the largest instance).
+struct CtaScratch {
+  double *x, *r, *rt, *p, *q, *uu, *vh, *H, *cprime, *partials, *g;
+  unsigned *bar;
+  double2 *SA, *SB, *SP, *Y1, *Y2;
+  float *x32, *r32, *rt32, *p32, *q32, *uu32, *vh32;
+  float2 *SA32, *SP32, *Y1f, *Y2f;
+};
+// Per-instance inputs of the batched setup (constant coefficients).
+struct InstanceSetup {
+  double alpha, beta, tau, h, gamma, d_plus, d_minus;
+  double *omega, *gtmp;
+  double2 *BhF;
+};
+struct BatchArgs {
+  int count;
+  const Args *inst;            // per-instance Args (per-CTA pointers patched in-kernel)
+  const InstanceSetup *setup;  // per-instance setup inputs
+  const CtaScratch *cta;       // per-CTA work arrays
+  const int *order;            // work-queue order (largest instances first)
+  unsigned *next;              // work-queue counter (zeroed before each launch)
+};
+
 // Host-side entry points implemented in level_kernels.cu.
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
@@ -309,6 +363,9 @@ int launch_time_tables(int M, double alpha, double tau, double h, double beta, c
                        double *q, double *kp, double *km, cudaStream_t st);
 size_t level_smem_bytes(const Args &A);
 const void *level_kernel_ptr();
+const void *batch_level_kernel_ptr();
+const void *batch_setup_kernel_ptr();
+int launch_batch(const BatchArgs &B, int grid, size_t smem, cudaStream_t st, int setup, int j0, int j1);
 const void *apply_kernel_ptr();
 const void *setup_kernel_ptr();
 
