@@ -207,6 +207,11 @@ int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, double *u_out, int64_t *l
 int tsfcde_batch_get_history(tsfcde_batch *b, int64_t i, int32_t *iters, double *resid, int64_t count);
 /* Every instance back to level 0 with its u^0 (device copy, no host transfer). */
 int tsfcde_batch_reset(tsfcde_batch *b);
+/* Replace every instance's u^0 with u0_all (host; the N_i values of instance 0, then 1, ...,
+ * concatenated: sum N_i doubles) and go back to level 0. */
+int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all);
+/* Copy every instance's current level to u_all (host, concatenated like u0_all). */
+int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all);
 /* Release everything.  NULL is allowed. */
 void tsfcde_batch_free(tsfcde_batch *b);
 

@@ -110,6 +110,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_batch_get_history.restype = C.c_int
     lib.tsfcde_batch_reset.argtypes = [vp]
     lib.tsfcde_batch_reset.restype = C.c_int
+    lib.tsfcde_batch_set_initial.argtypes = [vp, vp]
+    lib.tsfcde_batch_set_initial.restype = C.c_int
+    lib.tsfcde_batch_get_all.argtypes = [vp, vp]
+    lib.tsfcde_batch_get_all.restype = C.c_int
     lib.tsfcde_batch_free.argtypes = [vp]
     lib.tsfcde_batch_free.restype = None
     lib.tsfcde_free.argtypes = [vp]
@@ -332,6 +336,14 @@ class Batch:
 
     def reset(self):
         _check(self.lib.tsfcde_batch_reset(self.h), "tsfcde_batch_reset")
+
+    def set_initial(self, u0_ptr: int):
+        """New u^0 for every instance from the host address u0_ptr (sum N_i doubles)."""
+        _check(self.lib.tsfcde_batch_set_initial(self.h, u0_ptr), "tsfcde_batch_set_initial")
+
+    def get_all(self, u_ptr: int):
+        """Every instance's current level into the host address u_ptr (sum N_i doubles)."""
+        _check(self.lib.tsfcde_batch_get_all(self.h, u_ptr), "tsfcde_batch_get_all")
 
     def close(self):
         if getattr(self, "h", None):

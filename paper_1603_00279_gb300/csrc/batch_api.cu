@@ -29,7 +29,9 @@ struct tsfcde_batch {
   tsf::CtaScratch *d_cta = nullptr;
   int *d_order = nullptr;
   unsigned *d_next = nullptr;
-  double *d_u0 = nullptr;            // all instances' u^0, concatenated (L_i doubles each)
+  double *d_u0 = nullptr;            // all instances' u^0, concatenated (N_i doubles each)
+  double *d_uout = nullptr;          // staging for tsfcde_batch_get_all (same layout)
+  size_t u_total = 0;
   int grid = 0;
   size_t smem = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -198,6 +200,8 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       u0_total += (size_t)b->n[i];
     }
     b->d_u0 = cv.take<double>(u0_total);
+    b->d_uout = cv.take<double>(u0_total);
+    b->u_total = u0_total;
     if (!pass) {
       CK(cudaMalloc(&b->arena, cv.off + 256));
       CK(cudaMemsetAsync(b->arena, 0, cv.off + 256, b->stream));
@@ -354,6 +358,24 @@ int tsfcde_batch_reset(tsfcde_batch *b) {
                        cudaMemcpyDeviceToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   b->level = 0;
+  return TSFCDE_OK;
+}
+
+int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all) {
+  if (!b || !u0_all) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(b->device));
+  CK(cudaMemcpyAsync(b->d_u0, u0_all, b->u_total * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  return tsfcde_batch_reset(b);
+}
+
+int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all) {
+  if (!b || !u_all) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(b->device));
+  for (int64_t i = 0; i < b->count; ++i)
+    CK(cudaMemcpyAsync(b->d_uout + b->u0_off[i], b->inst[i].u, b->n[i] * sizeof(double),
+                       cudaMemcpyDeviceToDevice, b->stream));
+  CK(cudaMemcpyAsync(u_all, b->d_uout, b->u_total * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
   return TSFCDE_OK;
 }
 
