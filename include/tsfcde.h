@@ -56,17 +56,17 @@ extern "C" {
 
 #define TSFCDE_FP64 0  /* every step in float64                                             */
 #define TSFCDE_MIXED 1 /* iterative refinement: residual r = g - A x, solution update, history
-                          sum and all spectra/weights in float64; CGS on A d = r in float32
-                          (float32 FFTs, matvecs and preconditioner, spectra rounded from
-                          float64); a level whose float64 residual stops falling by half per
-                          refinement step, or whose float32 solve breaks down, is finished by
-                          the float64 CGS from the current iterate (counted as escalated)   */
+                          sum and all spectra/weights in float64; CGS on A d = r in float32 or
+                          float-float (FFTs, matvecs and preconditioner in that precision,
+                          spectra rounded from float64), chosen per level (inner_precision);
+                          see TSFCDE_INNER_AUTO for the stopping and escalation rules       */
 
 typedef struct tsfcde_options {
   int32_t precision;      /* TSFCDE_FP64 (default) or TSFCDE_MIXED                         */
   int32_t preconditioner; /* TSFCDE_PRECOND_*; default STRANG                               */
   double tol;             /* CGS stop: ||r_k||_2 / ||r_0||_2 < tol (Section 4); default 1e-12 */
-  int32_t maxit;          /* CGS iterations per level before E_NOT_CONVERGED; default 2000  */
+  int32_t maxit;          /* CGS iterations per level before E_NOT_CONVERGED; default 2000.
+                             A level that reaches it keeps its minimum-residual iterate.    */
   int32_t device;         /* CUDA device ordinal; default 0                                 */
   /* Separable source f(x,t) = sum_r T_r(t) X_r(x) (used when source_rank > 0, in which case the
    * f callback of tsfcde_setup must be NULL):
@@ -80,10 +80,26 @@ typedef struct tsfcde_options {
   void *stream;              /* cudaStream_t to run on (e.g. a PyTorch stream); NULL = the
                                 library creates and owns a non-blocking stream               */
   double inner_tol;          /* MIXED: relative residual of each float32 solve; default 1e-5  */
-  int32_t inner_maxit;       /* MIXED: float32 CGS iterations per refinement step; default 200 */
+  int32_t inner_maxit;       /* MIXED: inner CGS iterations per refinement step; default 1000 */
   int32_t outer_maxit;       /* MIXED: refinement steps per level before escalation; default 12 */
-  int32_t reserved[4];
+  int32_t barrier_spin_log2; /* a device-wide barrier wait gives up after 2^k polls and the call
+                                returns TSFCDE_E_TIMEOUT; default 23 (a few seconds)           */
+  int32_t test_skip_arrival; /* testing hook, 0 normally: when 1, CTA 0 skips its first barrier
+                                arrival in the next launch only, so every wait of that launch
+                                runs into its bound and the call returns TSFCDE_E_TIMEOUT     */
+  int32_t inner_precision;   /* MIXED inner solve: TSFCDE_INNER_AUTO (default), _FP32, _FF    */
+  int32_t reserved[1];
 } tsfcde_options;
+
+/* Inner precision of TSFCDE_MIXED.  AUTO estimates per level kappa_eff = max|A^| / eta_j <=
+ * 1 + sigma ((kappa_+ + kappa_-) 2|omega_1| + 2|q|) / eta_j (Remark 3.1 bounds the eigenvalues
+ * of s(W_beta) by 2|omega_1|) and runs the inner CGS in float32 when u32 * kappa_eff < 1e-3,
+ * otherwise in float-float (pairs of floats, ~48-bit significands, on the FP32 pipe).  A level
+ * whose float64 residual stops halving below 64 u64 kappa_eff (the float64 floor of r = g - Ax)
+ * is accepted; above that it is finished by the float64 CGS. */
+#define TSFCDE_INNER_AUTO 0
+#define TSFCDE_INNER_FP32 1
+#define TSFCDE_INNER_FF 2
 
 /* Fill `opt` with the defaults above (the paper's settings: Strang, tol 1e-12, x0 = 0). */
 void tsfcde_default_options(tsfcde_options *opt);

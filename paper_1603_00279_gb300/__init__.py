@@ -27,6 +27,7 @@ STATUS_NAMES = {
 }
 PRECONDITIONERS = {"strang": 0, "tchan": 1, "none": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+INNER = {"auto": 0, "fp32": 1, "ff": 2}
 OPS = {"A": 0, "B": 1, "Pinv": 2}
 
 COEF_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
@@ -40,7 +41,8 @@ class Options(C.Structure):
                 ("source_x", C.POINTER(C.c_double)), ("source_t", C.POINTER(C.c_double)),
                 ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("barrier_spin_log2", C.c_int32), ("test_skip_arrival", C.c_int32),
+                ("inner_precision", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Stats(C.Structure):
@@ -151,7 +153,8 @@ class Solver:
                  maxit: int = 2000, device: int = 0, levels_per_launch: int = 0,
                  stream: Optional[int] = None, precision: str = "fp64",
                  inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
-                 outer_maxit: Optional[int] = None):
+                 outer_maxit: Optional[int] = None, barrier_spin_log2: Optional[int] = None,
+                 test_skip_arrival: bool = False, inner: str = "auto"):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
         self.h = (b - a) / (N + 1)
@@ -188,6 +191,10 @@ class Solver:
             opt.inner_maxit = inner_maxit
         if outer_maxit is not None:
             opt.outer_maxit = outer_maxit
+        if barrier_spin_log2 is not None:
+            opt.barrier_spin_log2 = barrier_spin_log2
+        opt.test_skip_arrival = 1 if test_skip_arrival else 0
+        opt.inner_precision = INNER[inner]
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
@@ -291,7 +298,7 @@ class Batch:
 
     def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, inner: str = "auto"):
         self.lib = load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
@@ -311,6 +318,7 @@ class Batch:
         opt.precision = PRECISIONS[precision]
         opt.device = device
         opt.stream = stream
+        opt.inner_precision = INNER[inner]
         h = C.c_void_p()
         _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
                "tsfcde_batch_setup")

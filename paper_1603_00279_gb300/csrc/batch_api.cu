@@ -139,6 +139,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     A.inner_tol = b->opt.inner_tol;
     A.inner_maxit = b->opt.inner_maxit;
     A.outer_maxit = b->opt.outer_maxit;
+    A.spin_limit = 1ll << b->opt.barrier_spin_log2;
     b->n[i] = in[i].N;
     lgLmax = std::max(lgLmax, A.cp.lgL);
     nmax = std::max(nmax, in[i].N);
@@ -189,7 +190,12 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       A.outer_iters = cv.take<int>(M);
       A.escalated = cv.take<int>(M);
       A.status = cv.take<int>(4);
-      if (mixed) A.twL32 = cv.take<float2>(L);
+      A.lv_inner = cv.take<int>(M);
+      A.lv_floor = cv.take<double>(M);
+      if (mixed) {
+        A.twL32 = cv.take<float2>(L);
+        A.twLff = cv.take<tsf::ffc>(L);
+      }
     }
     b->u0_off.assign(K, 0);
     double *u0base = cv.take<double>(1);
@@ -223,6 +229,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       C.uu = cs.take<double>(Lmax);
       C.vh = cs.take<double>(Lmax);
       C.H = cs.take<double>(Lmax);
+      C.xb = cs.take<double>(Lmax);
       C.cprime = cs.take<double>(nmax);
       C.partials = cs.take<double>(8);
       C.bar = cs.take<unsigned>(tsf::kBarWords);
@@ -244,6 +251,17 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
         C.SP32 = cs.take<float2>(Nmax + 1);
         C.Y1f = cs.take<float2>(Nmax);
         C.Y2f = cs.take<float2>(Nmax);
+        C.xff = cs.take<tsf::ff>(Lmax);
+        C.rff = cs.take<tsf::ff>(Lmax);
+        C.rtff = cs.take<tsf::ff>(Lmax);
+        C.pff = cs.take<tsf::ff>(Lmax);
+        C.qff = cs.take<tsf::ff>(Lmax);
+        C.uuff = cs.take<tsf::ff>(Lmax);
+        C.vhff = cs.take<tsf::ff>(Lmax);
+        C.SAff = cs.take<tsf::ffc>(Nmax + 1);
+        C.SPff = cs.take<tsf::ffc>(Nmax + 1);
+        C.Y1ff = cs.take<tsf::ffc>(Nmax);
+        C.Y2ff = cs.take<tsf::ffc>(Nmax);
       }
     }
     if (!pass) {
@@ -278,6 +296,27 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
   CK(cudaMemcpyAsync(b->d_cta, cta.data(), b->grid * sizeof(tsf::CtaScratch), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->d_order, order.data(), K * sizeof(int), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->d_u0, u0all.data(), u0_total * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  // precision controller per instance and level (constant coefficients: j = 0 and j >= 1)
+  std::vector<int> inner_all((size_t)K * M);
+  std::vector<double> floor_all((size_t)K * M);
+  for (int64_t i = 0; i < K; ++i) {
+    const tsfcde_instance &I = in[i];
+    const double sigma = 1.0 - I.alpha / 2.0, tau = I.T / (double)M, h = (I.b - I.a) / (double)(I.N + 1);
+    const double a0 = std::pow(sigma, 1.0 - I.alpha);
+    const double b1 = (std::pow(1.0 + sigma, 2.0 - I.alpha) - std::pow(sigma, 2.0 - I.alpha)) / (2.0 - I.alpha) -
+                      0.5 * (std::pow(1.0 + sigma, 1.0 - I.alpha) + std::pow(sigma, 1.0 - I.alpha));
+    const double den = std::pow(tau, I.alpha) * std::tgamma(2.0 - I.alpha), hb = std::pow(h, I.beta);
+    for (int64_t j = 0; j < M; ++j) {
+      const double eta = (j == 0 ? a0 : a0 + b1) / den;
+      tsf::precision_control(sigma, I.beta, eta, I.gamma / (2.0 * h), I.d_plus / hb, I.d_minus / hb,
+                             b->opt.inner_precision, b->opt.tol, &inner_all[(size_t)i * M + j],
+                             &floor_all[(size_t)i * M + j]);
+    }
+    CK(cudaMemcpyAsync((void *)b->inst[i].lv_inner, inner_all.data() + (size_t)i * M, M * sizeof(int),
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync((void *)b->inst[i].lv_floor, floor_all.data() + (size_t)i * M, M * sizeof(double),
+                       cudaMemcpyHostToDevice, b->stream));
+  }
   CK(cudaStreamSynchronize(b->stream));
   // ---- device setup: weights, tables, spectra of every instance ----
   tsf::BatchArgs B;

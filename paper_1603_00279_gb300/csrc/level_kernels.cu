@@ -163,7 +163,10 @@ __device__ __forceinline__ void store_ab(const Args &A, const LevelScalars &s, i
   ab_symbols(A, s, __ldg(A.twL + k), nyq, A.What[slot], sa, sb);
   A.SA[slot] = sa;
   A.SB[slot] = sb;
-  if (A.precision == kMixed) A.SA32[slot] = to_f2(sa);
+  if (A.precision == kMixed) {
+    A.SA32[slot] = to_f2(sa);
+    A.SAff[slot] = to_ffc(sa);
+  }
 }
 
 template <int MODE, typename T>
@@ -238,8 +241,15 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
         if (k == 0) Sout[N] = vn;
         if (A.precision == kMixed && sym_level >= 0 && Sout == A.SP) {
           A.SP32[sk] = to_f2(v0);
-          if (!self) A.SP32[sp] = to_f2(v1);
-          if (k == 0) A.SP32[N] = to_f2(vn);
+          A.SPff[sk] = to_ffc(v0);
+          if (!self) {
+            A.SP32[sp] = to_f2(v1);
+            A.SPff[sp] = to_ffc(v1);
+          }
+          if (k == 0) {
+            A.SP32[N] = to_f2(vn);
+            A.SPff[N] = to_ffc(vn);
+          }
         }
         if (sym_level >= 0) {
           store_ab(A, ls, sk, k, false);
@@ -489,6 +499,7 @@ __device__ void ph_commit(const Args &A, int j) {
 template <typename T>
 struct Krylov {
   typename RealOf<T>::R *x, *r, *rt, *p, *q, *uu, *vh;
+  typename RealOf<T>::R *xb;   // minimum-residual iterate (kept when non-null)
   const T *SA, *SP;
   T *Y1, *Y2;
   const T *twG;
@@ -513,13 +524,19 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
   double tot[3];
   bool first = true;
   double beta = 0.0;
+  double best = 1.0;       // smallest ||r_k|| / nref so far (the start has 1 when x0 = 0)
+  bool save = false;       // the iterate after the last iteration is the best so far
+  bool have = false;       // a best iterate has been copied to xb
   while (true) {
     ++its;
     if (!first) {
       const R bt = (R)beta;
-      // u = r + beta q; p = u + beta (q + beta p); forward transform of p
+      const bool keep = save && V.xb != nullptr;
+      have = have || keep;
+      // u = r + beta q; p = u + beta (q + beta p); forward transform of p; keep the best x
       col_pass<false, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, V.Y1,
                                [&](int m, T) -> T {
+                                 if (keep) stp<T>(V.xb, m, ldp<T>(V.x, m));
                                  const T rv = ldp<T>(V.r, m), qv = ldp<T>(V.q, m), pv = ldp<T>(V.p, m);
                                  T uv, pn;
                                  mkc(uv, rv.x + bt * qv.x, rv.y + bt * qv.y);
@@ -624,7 +641,21 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
     rel = sqrt(tot[1]) / nref;
     if (!(rel == rel) || isinf(rel)) return kENonFinite;
     if (rel < tol) return kOK;
-    if (its >= maxit) return kENotConverged;
+    save = rel < best;
+    if (save) best = rel;
+    if (its >= maxit) {
+      // like MATLAB's cgs: a solve that does not converge returns its minimum-residual iterate
+      if (V.xb != nullptr && !save && have) {
+        col_pass<false, false, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, nullptr,
+                                  [&](int m, T z) -> T {
+                                    stp<T>(V.x, m, ldp<T>(V.xb, m));
+                                    return z;
+                                  });
+        if (!(alive = grid_sync(A))) return kOK;
+        rel = best;
+      }
+      return kENotConverged;
+    }
     if (tot[0] == 0.0) return kEBreakdown;
     beta = tot[0] / rho;
     rho = tot[0];
@@ -634,6 +665,38 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
 // ------------------------------------------------------------------------------------------------
 // the level kernel
 // ------------------------------------------------------------------------------------------------
+// Start of an inner solve on A d = r: d = 0, r = r~ = u = p = r rounded to the inner type;
+// returns this element pair's contribution to (r, r) in the inner type.
+__device__ __forceinline__ double inner_start(const Args &A, bool useff, int m, double2 rv) {
+  if (useff) {
+    const ffc r = to_ffc(rv);
+    ffc z;
+    z.x = ff(0.0);
+    z.y = ff(0.0);
+    stp<ffc>(A.xff, m, z);
+    stp<ffc>(A.rff, m, r);
+    stp<ffc>(A.rtff, m, r);
+    stp<ffc>(A.uuff, m, r);
+    stp<ffc>(A.pff, m, r);
+    return (double)(r.x * r.x + r.y * r.y);
+  }
+  const float2 r32 = to_f2(rv);
+  stp<float2>(A.x32, m, make_float2(0.f, 0.f));
+  stp<float2>(A.r32, m, r32);
+  stp<float2>(A.rt32, m, r32);
+  stp<float2>(A.uu32, m, r32);
+  stp<float2>(A.p32, m, r32);
+  return (double)(r32.x * r32.x + r32.y * r32.y);
+}
+__device__ __forceinline__ double2 inner_solution(const Args &A, bool useff, int m) {
+  if (useff) {
+    const ffc d = ldp<ffc>(A.xff, m);
+    return make_double2((double)d.x, (double)d.y);
+  }
+  const float2 d = ldp<float2>(A.x32, m);
+  return make_double2((double)d.x, (double)d.y);
+}
+
 // March levels [j0, j1) of one instance with the current team (whole grid or one CTA).
 __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   const int n = A.n;
@@ -641,15 +704,22 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   int rb = 0;
   Krylov<double2> V64;
   V64.x = A.x; V64.r = A.r; V64.rt = A.rt; V64.p = A.p; V64.q = A.q; V64.uu = A.uu; V64.vh = A.vh;
+  V64.xb = A.xb;
   V64.SA = A.SA; V64.SP = A.SP; V64.Y1 = A.Y1; V64.Y2 = A.Y2; V64.twG = A.twL;
   Krylov<float2> V32;
   V32.x = A.x32; V32.r = A.r32; V32.rt = A.rt32; V32.p = A.p32; V32.q = A.q32; V32.uu = A.uu32;
+  V32.xb = nullptr;
   V32.vh = A.vh32; V32.SA = A.SA32; V32.SP = A.SP32; V32.Y1 = A.Y1f; V32.Y2 = A.Y2f; V32.twG = A.twL32;
+  Krylov<ffc> VF;
+  VF.x = A.xff; VF.r = A.rff; VF.rt = A.rtff; VF.p = A.pff; VF.q = A.qff; VF.uu = A.uuff;
+  VF.xb = nullptr;
+  VF.vh = A.vhff; VF.SA = A.SAff; VF.SP = A.SPff; VF.Y1 = A.Y1ff; VF.Y2 = A.Y2ff; VF.twG = A.twLff;
 
   for (int j = j0; j < j1; ++j) {
     if (j == j0 || A.lv_newsym[j]) {
       if (!level_symbols(A, S, j)) return;
     }
+    const bool useff = mixed && A.lv_inner[j] != 0;
     // ---- RHS: g = B u^j - hscale * H^j + f^{j+sigma} (Eq. (3.1)) ----
     const bool commit = j > j0;
     ph_history(A, j, commit);
@@ -684,13 +754,7 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
                                     st2(A.r, m, g);
                                     if (mixed) {
                                       st2(A.g, m, g);
-                                      const float2 g32 = to_f2(g);
-                                      stp<float2>(A.x32, m, make_float2(0.f, 0.f));
-                                      stp<float2>(A.r32, m, g32);
-                                      stp<float2>(A.rt32, m, g32);
-                                      stp<float2>(A.uu32, m, g32);
-                                      stp<float2>(A.p32, m, g32);
-                                      acc[1] += (double)(g32.x * g32.x + g32.y * g32.y);
+                                      acc[1] += inner_start(A, useff, m, g);
                                     } else {
                                       st2(A.rt, m, g);
                                       st2(A.uu, m, g);
@@ -719,8 +783,10 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
       while (true) {
         int ii = 0;
         double irel = 0.0;
-        const int ist = cgs_solve<float2>(A, S, V32, rho32, sqrt(rho32), A.inner_tol, A.inner_maxit,
-                                          false, rb, ii, irel, alive);
+        const int ist = useff ? cgs_solve<ffc>(A, S, VF, rho32, sqrt(rho32), A.inner_tol, A.inner_maxit,
+                                                false, rb, ii, irel, alive)
+                              : cgs_solve<float2>(A, S, V32, rho32, sqrt(rho32), A.inner_tol,
+                                                  A.inner_maxit, false, rb, ii, irel, alive);
         if (!alive) return;
         its += ii;
         ++outer;
@@ -730,8 +796,8 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
                                        [&](int m, double2) -> double2 {
                                          double2 xv = ld2(A.x, m);
                                          if (inner_ok) {
-                                           const float2 dv = ldp<float2>(A.x32, m);
-                                           xv = make_double2(xv.x + (double)dv.x, xv.y + (double)dv.y);
+                                           const double2 dv = inner_solution(A, useff, m);
+                                           xv = make_double2(xv.x + dv.x, xv.y + dv.y);
                                            st2(A.x, m, xv);
                                          }
                                          return xv;
@@ -752,13 +818,7 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
                                          st2(A.rt, m, rv);
                                          st2(A.uu, m, rv);
                                          st2(A.p, m, rv);
-                                         const float2 r32 = to_f2(rv);
-                                         stp<float2>(A.x32, m, make_float2(0.f, 0.f));
-                                         stp<float2>(A.r32, m, r32);
-                                         stp<float2>(A.rt32, m, r32);
-                                         stp<float2>(A.uu32, m, r32);
-                                         stp<float2>(A.p32, m, r32);
-                                         acc[1] += (double)(r32.x * r32.x + r32.y * r32.y);
+                                         acc[1] += inner_start(A, useff, m, rv);
                                          return z;
                                        });
         write_partials(A, S, rb, acc);
@@ -769,7 +829,9 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
         rho32 = tot[1];
         if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
         if (rel < A.tol) break;
-        // no progress (or diverging) in FP32 -> finish the level with the FP64 CGS from x
+        // stagnation at the FP64 residual floor (about u64 * kappa_eff) is convergence
+        if (inner_ok && rel > 0.5 * prev && rel < A.lv_floor[j]) break;
+        // no progress (or diverging) in the inner precision -> finish with the FP64 CGS from x
         if (!inner_ok || rel > 0.5 * prev || outer >= A.outer_maxit) {
           esc = 1;
           int i64 = 0;
@@ -857,7 +919,10 @@ __device__ void setup_body(const Args &A, const SetupArgs &T, const Smem &S) {
     double s, c;
     sincospi(-2.0 * (double)k / (double)L, &s, &c);
     T.twL[k] = make_double2(c, s);
-    if (A.precision == kMixed) A.twL32[k] = make_float2((float)c, (float)s);
+    if (A.precision == kMixed) {
+      A.twL32[k] = make_float2((float)c, (float)s);
+      A.twLff[k] = to_ffc(make_double2(c, s));
+    }
   }
   for (int k = gt; k < n; k += gs) {
     const long long k2 = ((long long)k * (long long)k) % (2ll * n);
@@ -928,10 +993,13 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void patch_cta_scratch(Args &A, const CtaScratch &C) {
   A.x = C.x; A.r = C.r; A.rt = C.rt; A.p = C.p; A.q = C.q; A.uu = C.uu; A.vh = C.vh; A.H = C.H;
+  A.xb = C.xb;
   A.SA = C.SA; A.SB = C.SB; A.SP = C.SP; A.Y1 = C.Y1; A.Y2 = C.Y2; A.cprime = C.cprime;
   A.partials = C.partials; A.bar = C.bar;
   A.g = C.g; A.x32 = C.x32; A.r32 = C.r32; A.rt32 = C.rt32; A.p32 = C.p32; A.q32 = C.q32;
   A.uu32 = C.uu32; A.vh32 = C.vh32; A.SA32 = C.SA32; A.SP32 = C.SP32; A.Y1f = C.Y1f; A.Y2f = C.Y2f;
+  A.xff = C.xff; A.rff = C.rff; A.rtff = C.rtff; A.pff = C.pff; A.qff = C.qff; A.uuff = C.uuff;
+  A.vhff = C.vhff; A.SAff = C.SAff; A.SPff = C.SPff; A.Y1ff = C.Y1ff; A.Y2ff = C.Y2ff;
 }
 
 // One instance's weights (Lemma 2) and level tables (Lemma 1) with a one-CTA team; constant
@@ -1380,6 +1448,7 @@ extern "C" int tsfcde_apply_operator_static(int64_t N, double beta, double sigma
   A.bp.lg1 = 1;   // no complex-plan phases run here
   A.bp.lg2 = 1;
   A.sigma = sigma;
+  A.spin_limit = kSpinLimit;
   const int G = std::min(d->sms, kMaxGrid);
   auto cap = [&](int items, int lines_per_item, int lg) {
     const int per = (items + G - 1) / G;

@@ -21,7 +21,7 @@
 namespace tsf {
 
 constexpr int kThreads = 256;                 // threads per CTA of every kernel
-constexpr long long kSpinLimit = 1ll << 23;   // bound on a barrier wait (about 2-4 s)
+constexpr long long kSpinLimit = 1ll << 23;   // default bound on a barrier wait (a few seconds)
 
 // status codes (mirror include/tsfcde.h)
 constexpr int kOK = 0, kEInvalid = 1, kENoMem = 2, kECuda = 3, kENonFinite = 4,
@@ -34,6 +34,9 @@ struct ConvPlan {  // real length L, complex length N = L/2 = N1 * N2
 struct CplxPlan {  // complex length Nc = L = N1 * N2
   int Nc, lgNc, N1, lg1, N2, lg2;
 };
+
+struct ff;    // float-float real (defined below)
+struct ffc;   // float-float complex
 
 // Everything a device kernel needs, passed by value.
 struct Args {
@@ -62,6 +65,7 @@ struct Args {
   const double *f_dense;  // M x n or null
   // state
   double *u, *x, *r, *rt, *p, *q, *uu, *vh, *H;
+  double *xb;             // minimum-residual iterate of the FP64 CGS
   double *ring;
   long long ring_stride;
   double2 *SA, *SB, *SP;  // per-level spectra (permuted, N+1), scaled by 1/(4N)
@@ -83,6 +87,15 @@ struct Args {
   float2 *twL32;          // FP32 twiddles (rounded from the FP64 table)
   int *outer_iters;       // M: refinement steps per level
   int *escalated;         // M: 1 if the level fell back to FP64 CGS
+  long long spin_limit;   // polls before a barrier wait gives up
+  int test_skip;          // testing hook: CTA 0 skips its first barrier arrival
+  // float-float inner solve (mixed mode, levels where FP32 cannot resolve the operator)
+  const int *lv_inner;    // per level: 0 FP32 inner solve, 1 float-float inner solve
+  const double *lv_floor; // per level: FP64 residual accepted once refinement stagnates below it
+  ff *xff, *rff, *rtff, *pff, *qff, *uuff, *vhff;   // float-float Krylov vectors (L each)
+  ffc *SAff, *SPff;       // float-float spectra (rounded from FP64), N+1
+  ffc *Y1ff, *Y2ff;       // float-float FFT work, L/2 each
+  ffc *twLff;             // float-float twiddles, L
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -114,9 +127,78 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
 
+// ---------------------------------------------------------------------------------------------
+// float-float numbers (an unevaluated sum hi + lo of two floats, |lo| <= ulp(hi)/2): about 48-bit
+// significands computed on the FP32 pipe.  Error-free transformations after Dekker and Knuth
+// (TwoSum, FastTwoSum) and the FMA-based product; additions use the "sloppy" form
+// (s, e) = TwoSum(a.hi, b.hi); e += a.lo + b.lo; renormalise -- relative error about 2^-46 of
+// |a| + |b|, which is what FFT butterflies and axpy updates need.
+// ---------------------------------------------------------------------------------------------
+struct __align__(8) ff {
+  float hi, lo;
+  __device__ __forceinline__ ff() {}
+  __device__ __forceinline__ ff(double d) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+  }
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return ff(s, e);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_fast_two_sum(s, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return ff_sub(a, b); }
+__device__ __forceinline__ ff operator*(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ ff operator-(ff a) { return ff_neg(a); }
+__device__ __forceinline__ ff &operator+=(ff &a, ff b) { a = ff_add(a, b); return a; }
+
+struct __align__(16) ffc {   // complex float-float
+  ff x, y;
+};
+__device__ __forceinline__ ffc cadd(ffc a, ffc b) { ffc r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+__device__ __forceinline__ ffc csub(ffc a, ffc b) { ffc r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+__device__ __forceinline__ ffc cmul(ffc a, ffc b) {
+  ffc r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+__device__ __forceinline__ ffc cmulc(ffc a, ffc b) {
+  ffc r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+__device__ __forceinline__ ffc cconj(ffc a) { ffc r; r.x = a.x; r.y = -a.y; return r; }
+__device__ __forceinline__ ffc mul_i(ffc a) { ffc r; r.x = -a.y; r.y = a.x; return r; }
+__device__ __forceinline__ ffc mul_mi(ffc a) { ffc r; r.x = a.y; r.y = -a.x; return r; }
+__device__ __forceinline__ void mkc(ffc &z, ff x, ff y) { z.x = x; z.y = y; }
+__device__ __forceinline__ ffc to_ffc(double2 v) { ffc r; r.x = ff(v.x); r.y = ff(v.y); return r; }
+
 template <typename T> struct RealOf;
 template <> struct RealOf<double2> { using R = double; };
 template <> struct RealOf<float2> { using R = float; };
+template <> struct RealOf<ffc> { using R = ff; };
 __device__ __forceinline__ void mkc(double2 &z, double x, double y) { z = make_double2(x, y); }
 __device__ __forceinline__ void mkc(float2 &z, float x, float y) { z = make_float2(x, y); }
 
@@ -284,10 +366,10 @@ __device__ __forceinline__ bool grid_sync(const Args &A) {
     const unsigned long long k = ++bar_count();
     const unsigned long long target = k * (unsigned long long)gridDim.x;
     __threadfence();
-    red_add_release_u64(cnt, 1ull);
+    if (!(A.test_skip && blockIdx.x == 0 && k == 1)) red_add_release_u64(cnt, 1ull);
     long long spins = 0;
     while (ld_acquire_u64(cnt) < target) {
-      if (++spins > kSpinLimit) {
+      if (++spins > A.spin_limit) {
         raise_fatal(A, kETimeout);
         break;
       }
@@ -327,13 +409,34 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double *sm /* K*32 dou
   __syncthreads();
 }
 
+// Host-side precision controller of the mixed mode: for level j with eta_j, q, kappa_pm
+// returns the inner type (0 FP32, 1 float-float) and the FP64 residual floor.
+inline void precision_control(double sigma, double beta, double eta, double q, double kp, double km,
+                              int inner_opt, double tol, int *inner, double *floor_out) {
+  const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
+  const double lam0 = (4.0 - beta * beta) / 6.0;
+  const double w1 = lam0 - beta * lam1;   // omega_1 = lambda_1 g_1 + lambda_0 g_0
+  const double ab = (w1 < 0 ? -w1 : w1);
+  const double qa = (q < 0 ? -q : q);
+  const double kappa = 1.0 + sigma * ((kp + km) * 2.0 * ab + 2.0 * qa) / eta;
+  const double u32 = 5.9604644775390625e-08, u64 = 1.1102230246251565e-16;
+  int t = (u32 * kappa < 1e-3) ? 0 : 1;
+  if (inner_opt == 1) t = 0;
+  if (inner_opt == 2) t = 1;
+  *inner = t;
+  const double fl = 64.0 * u64 * kappa;
+  *floor_out = fl > tol ? fl : tol;
+}
+
 // Per-CTA work arrays of the batched solver (sized for the largest instance).
 struct CtaScratch {
-  double *x, *r, *rt, *p, *q, *uu, *vh, *H, *cprime, *partials, *g;
+  double *x, *r, *rt, *p, *q, *uu, *vh, *H, *cprime, *partials, *g, *xb;
   unsigned *bar;
   double2 *SA, *SB, *SP, *Y1, *Y2;
   float *x32, *r32, *rt32, *p32, *q32, *uu32, *vh32;
   float2 *SA32, *SP32, *Y1f, *Y2f;
+  ff *xff, *rff, *rtff, *pff, *qff, *uuff, *vhff;
+  ffc *SAff, *SPff, *Y1ff, *Y2ff;
 };
 // Per-instance inputs of the batched setup (constant coefficients).
 struct InstanceSetup {

@@ -50,10 +50,33 @@ def test_mixed_matches_fp64_gpu_path():
 
 
 def test_mixed_escalates_when_fp32_cannot_converge():
-    """beta = 1.9, alpha = 0.3 at n = 4095: u32 * kappa_eff ~ 0.3, the FP32 inner solve cannot
-    make progress; such levels must be finished by the FP64 CGS and still match FP64."""
+    """beta = 1.9, alpha = 0.3 at n = 4095 with the inner solve forced to FP32: u32 * kappa_eff
+    ~ 0.3, FP32 cannot make progress; such levels must be finished by the FP64 CGS and still
+    match FP64."""
     P = solver_module()
     prob = W.config_large(n=4095, M=1024, preconditioner="strang")
     a, _ = _levels(P, prob, 6, precision="fp64")
-    b, st = _levels(P, prob, 6, precision="mixed")
+    b, st = _levels(P, prob, 6, precision="mixed", inner="fp32")
     assert max(rel_l2(b[j], a[j]) for j in range(7)) <= 1e-8
+    assert sum(s["escalated_levels"] for s in st) >= 1
+
+
+@pytest.mark.parametrize("n,precond", [(4095, "strang"), (4095, "tchan"), (65535, "strang")])
+def test_float_float_inner_where_fp32_fails(n, precond):
+    """Same operator family (beta = 1.9), float-float inner solve: no escalation, and the result
+    matches the FP64 GPU path to 1e-8."""
+    P = solver_module()
+    prob = W.config_large(n=n, M=1024, preconditioner=precond)
+    a, _ = _levels(P, prob, 4, precision="fp64")
+    b, st = _levels(P, prob, 4, precision="mixed", inner="ff")
+    assert max(rel_l2(b[j], a[j]) for j in range(5)) <= 1e-8
+    assert sum(s["escalated_levels"] for s in st) == 0
+
+
+def test_float_float_small_config_every_level():
+    P = solver_module()
+    prob = W.config_small()
+    ref = O.run(prob)
+    got, st = _levels(P, prob, prob.M, precision="mixed", inner="ff")
+    assert max(rel_l2(got[j], ref[j]) for j in range(prob.M + 1)) <= 1e-8
+    assert sum(s["escalated_levels"] for s in st) == 0
