@@ -37,6 +37,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 FMA/clk x 2 flop x max clock
 
 
+def hbm_peak():
+    """Measured copy bandwidth (MEASURED_PEAKS.json) or the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (profiling recipe)"
+
+
 def roofline(kernel, flops, kernel_ms, precision, outer_steps=0):
     """Roofline entry of the dominant kernel.  FP64: algorithmic FP64 flops against the FP64
     pipe.  Mixed: the inner solve runs on the FP32 pipe (FP32 or float-float arithmetic), so the
@@ -259,7 +268,9 @@ def run_native(args, p):
 
     stream = torch.cuda.Stream()
     s = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
-                              maxit=args.maxit, precision=args.precision)
+                              maxit=args.maxit, precision=args.precision,
+                              autotune=not args.no_autotune)
+    plan = s.plan()
     n, M = p.n, p.M
 
     def one_step():
@@ -300,6 +311,29 @@ def run_native(args, p):
         outer = sum(st["outer_iterations"] for st in stats) / max(1, len(stats))
         flops += outer * (5.0 * L * math.log2(L) + 3.0 * L)
 
+    # the history phase alone at the last level (reads all M-1 committed increments)
+    hist = None
+    if M >= 2:
+        jh = M - 1
+        for _ in range(2):
+            s.history_sum(jh, want=False)
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        h0.record(stream)
+        for _ in range(reps):
+            s.history_sum(jh, want=False)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        hms = h0.elapsed_time(h1) / reps
+        hbytes = 8.0 * n * jh + 16.0 * n
+        peak = hbm_peak()
+        hist = {"kernel": "history phase (level M-1)", "bound": "hbm",
+                "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
+                "frac": hbytes / (hms / 1e3) / 1e9 / peak[0], "traffic": None,
+                "ms": hms, "fp64_tflops": 2.0 * n * jh / (hms / 1e3) / 1e12,
+                "peak_source": peak[1]}
+
     # end to end through the C ABI with pinned host buffers: H2D of u^0, D2H of u^M per step
     u0 = torch.from_numpy(np.ascontiguousarray(p.phi(p.grid()))).pin_memory()
     uM = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -332,12 +366,13 @@ def run_native(args, p):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 inner / f64 refinement",
         "data": "synthetic (manufactured solution u=(t^2+1)x^2(1-x)^2, analytic source)",
-        "config": {**describe(p), "parallelism": f"replicas{world}",
+        "config": {**describe(p), "parallelism": f"replicas{world}", "fft_plan": plan,
                    "l2": "inputs larger than L2 (history ring %.0f MB)" % (M * n * 8 / 1e6)},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "roofline": roofline("level_kernel", flops, kernel_ms, args.precision),
+        "history_roofline": hist,
         "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max()),
                            "levels_at_maxit": int((it >= args.maxit).sum())},
         "max_level_residual": float(res.max()),
@@ -468,6 +503,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--instances", type=int, default=4096, help="batch workload: instance count")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the setup-time FFT-plan tuner")
     args = ap.parse_args()
     global _ARGS
     _ARGS = args

@@ -88,7 +88,10 @@ typedef struct tsfcde_options {
                                 arrival in the next launch only, so every wait of that launch
                                 runs into its bound and the call returns TSFCDE_E_TIMEOUT     */
   int32_t inner_precision;   /* MIXED inner solve: TSFCDE_INNER_AUTO (default), _FP32, _FF    */
-  int32_t reserved[1];
+  int32_t autotune;          /* 1: at setup, time the candidate FFT splits N/2 = N1 x N2 (N1 =
+                                N2/2, N2, 2 N2) and per-pass chunk sizes on the level operator
+                                product and keep the fastest (see tsfcde_get_plan); 0: default
+                                plan (N1 <= N2, N1 >= N2/2, chunks of 4096 values)            */
 } tsfcde_options;
 
 /* Inner precision of TSFCDE_MIXED.  AUTO estimates per level kappa_eff = max|A^| / eta_j <=
@@ -230,6 +233,18 @@ int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all);
 int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all);
 /* Release everything.  NULL is allowed. */
 void tsfcde_batch_free(tsfcde_batch *b);
+
+/* The FFT plan in use: the split N/2 = N1 x N2 of the half-length transform, the per-pass chunk
+ * budget (complex values per shared-memory buffer), and the autotuner's best time per operator
+ * product in microseconds (0 when autotune was off).  Any pointer may be NULL. */
+int tsfcde_get_plan(tsfcde_ctx *ctx, int32_t *N1, int32_t *N2, int32_t *budget, double *best_us);
+
+/* Diagnostic: the history sum of Lemma 1 for level j, H_i = sum_{s<j} c^{(j)}_{j-s} (u^{s+1}_i -
+ * u^s_i) (before the scaling tau^-alpha / Gamma(2-alpha)), computed by the same device phase the
+ * march uses, in its own launch with the march's launch shape.  Requires 1 <= j <= current level
+ * (the increments up to level j must be committed).  H_out: N host values, or NULL (device work
+ * only, e.g. for timing).  Does not change the march state. */
+int tsfcde_history_sum(tsfcde_ctx *ctx, int64_t j, double *H_out);
 
 /* Release everything the context holds.  NULL is allowed. */
 void tsfcde_free(tsfcde_ctx *ctx);

@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
                 ("barrier_spin_log2", C.c_int32), ("test_skip_arrival", C.c_int32),
-                ("inner_precision", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("inner_precision", C.c_int32), ("autotune", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -98,6 +98,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_reset.restype = C.c_int
     lib.tsfcde_get_history.argtypes = [vp, C.POINTER(i32), pd, i64]
     lib.tsfcde_get_history.restype = C.c_int
+    lib.tsfcde_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), pd]
+    lib.tsfcde_get_plan.restype = C.c_int
+    lib.tsfcde_history_sum.argtypes = [vp, i64, pd]
+    lib.tsfcde_history_sum.restype = C.c_int
     lib.tsfcde_apply.argtypes = [vp, i32, i64, pd, pd]
     lib.tsfcde_apply.restype = C.c_int
     lib.tsfcde_apply_operator_static.argtypes = [i64, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, vp, vp]
@@ -154,7 +158,7 @@ class Solver:
                  stream: Optional[int] = None, precision: str = "fp64",
                  inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
                  outer_maxit: Optional[int] = None, barrier_spin_log2: Optional[int] = None,
-                 test_skip_arrival: bool = False, inner: str = "auto"):
+                 test_skip_arrival: bool = False, inner: str = "auto", autotune: bool = False):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
         self.h = (b - a) / (N + 1)
@@ -195,6 +199,7 @@ class Solver:
             opt.barrier_spin_log2 = barrier_spin_log2
         opt.test_skip_arrival = 1 if test_skip_arrival else 0
         opt.inner_precision = INNER[inner]
+        opt.autotune = 1 if autotune else 0
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
@@ -264,6 +269,21 @@ class Solver:
         _check(self.lib.tsfcde_get_history(self.ctx, it.ctypes.data_as(C.POINTER(C.c_int32)),
                                            _dptr(rs), count), "tsfcde_get_history")
         return it, rs
+
+    def plan(self) -> dict:
+        """The FFT plan in use (autotuner's choice when autotune was requested)."""
+        n1, n2, b = C.c_int32(), C.c_int32(), C.c_int32()
+        us = C.c_double()
+        _check(self.lib.tsfcde_get_plan(self.ctx, C.byref(n1), C.byref(n2), C.byref(b), C.byref(us)),
+               "tsfcde_get_plan")
+        return {"N1": n1.value, "N2": n2.value, "budget": b.value, "best_us": us.value}
+
+    def history_sum(self, j: int, want: bool = True):
+        """Lemma 1 history sum of level j (unscaled), by the march's device phase."""
+        out = np.empty(self.N) if want else None
+        _check(self.lib.tsfcde_history_sum(self.ctx, j, _dptr(out) if want else None),
+               "tsfcde_history_sum")
+        return out
 
     def apply(self, op: str, j: int, x: np.ndarray) -> np.ndarray:
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -37,6 +37,8 @@ struct tsfcde_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<int> lv_inner;
   std::vector<double> lv_floor;
+  int budget = 4096;
+  double tune_best_us = 0.0;
 };
 
 namespace {
@@ -92,6 +94,27 @@ int reset_device_flags(tsfcde_ctx *c) {
   return TSFCDE_OK;
 }
 
+// Split of the half-length FFT, N = N1 x N2 with N1 = 2^lg1 (columns of N1 points).
+void set_split(Args &A, int lg1) {
+  A.cp.lg1 = lg1;
+  A.cp.lg2 = A.cp.lgN - lg1;
+  A.cp.N1 = 1 << A.cp.lg1;
+  A.cp.N2 = 1 << A.cp.lg2;
+}
+
+// Lines per CTA chunk in each pass kind for a grid of G CTAs and a per-buffer budget.
+void set_caps(Args &A, int G, int budget) {
+  auto cap = [&](int items, int lines_per_item, int lg) {
+    const int per = (items + G - 1) / G;
+    const int fit = std::max(1, (budget >> lg) / lines_per_item);
+    return std::max(1, std::min(per, fit));
+  };
+  A.cap_col = cap(A.cp.N2, 1, A.cp.lg1);
+  A.cap_row = cap(A.cp.N1 / 2 + 1, 2, A.cp.lg2);
+  A.cap_bcol = cap(A.bp.N2, 1, A.bp.lg1);
+  A.cap_brow = cap(A.bp.N1, 1, A.bp.lg2);
+}
+
 }  // namespace
 
 extern "C" {
@@ -113,6 +136,7 @@ void tsfcde_default_options(tsfcde_options *opt) {
   opt->barrier_spin_log2 = 23;
   opt->test_skip_arrival = 0;
   opt->inner_precision = TSFCDE_INNER_AUTO;
+  opt->autotune = 0;
 }
 
 const char *tsfcde_strerror(int status) {
@@ -190,10 +214,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   A.cp.L = 1 << lgL;
   A.cp.lgN = lgL - 1;
   A.cp.N = 1 << A.cp.lgN;
-  A.cp.lg1 = A.cp.lgN / 2;
-  A.cp.lg2 = A.cp.lgN - A.cp.lg1;
-  A.cp.N1 = 1 << A.cp.lg1;
-  A.cp.N2 = 1 << A.cp.lg2;
+  set_split(A, A.cp.lgN / 2);
   A.bp.lgNc = lgL;
   A.bp.Nc = 1 << lgL;
   A.bp.lg1 = lgL / 2;
@@ -219,24 +240,22 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, c->device));
   c->grid = std::min(prop.multiProcessorCount, tsf::kMaxGrid);
-  const int G = c->grid;
-  const int budget = 4096;   // complex values per ping-pong buffer
-  auto cap = [&](int items, int lines_per_item, int lg) {
-    const int per = (items + G - 1) / G;
-    const int fit = std::max(1, (budget >> lg) / lines_per_item);
-    return std::max(1, std::min(per, fit));
-  };
-  A.cap_col = cap(A.cp.N2, 1, A.cp.lg1);
-  A.cap_row = cap(A.cp.N1 / 2 + 1, 2, A.cp.lg2);
-  A.cap_bcol = cap(A.bp.N2, 1, A.bp.lg1);
-  A.cap_brow = cap(A.bp.N1, 1, A.bp.lg2);
+  c->budget = 4096;
+  set_caps(A, c->grid, c->budget);
   c->smem = tsf::level_smem_bytes(A);
   if (c->smem > prop.sharedMemPerBlockOptin) return TSFCDE_E_INVALID_ARG;
-  for (const void *fn : {tsf::level_kernel_ptr(), tsf::apply_kernel_ptr(), tsf::setup_kernel_ptr()}) {
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
-    if (occ < 1) return TSFCDE_E_INVALID_ARG;
+  const size_t smem_limit = prop.sharedMemPerBlockOptin;
+  {
+    // the attribute covers every plan the autotuner may try
+    const size_t smax = std::min(smem_limit, (size_t)(2 * 4096 + 4096) * sizeof(double2) + 4096);
+    for (const void *fn : {tsf::level_kernel_ptr(), tsf::apply_kernel_ptr(), tsf::setup_kernel_ptr(),
+                           tsf::history_kernel_ptr()}) {
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)std::max(smax, c->smem)));
+      int occ = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
+      if (occ < 1) return TSFCDE_E_INVALID_ARG;
+    }
   }
 
   // ---- device memory: one arena + the history ring ----
@@ -286,7 +305,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     c->gam = cv.take<double>(M);
     c->dp = cv.take<double>(M);
     c->dm = cv.take<double>(M);
-    A.partials = cv.take<double>((size_t)2 * G * 4);
+    A.partials = cv.take<double>((size_t)2 * c->grid * 4);
     A.bar = cv.take<unsigned>(tsf::kBarWords);
     A.status = cv.take<int>(4);
     A.iters = cv.take<int>(M);
@@ -381,17 +400,64 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
                                (double *)A.hc, (double *)A.hl, (double *)A.lv_eta, (double *)A.lv_q,
                                (double *)A.lv_kp, (double *)A.lv_km, c->stream);
   if (st) return st;
-  st = reset_device_flags(c);
+  auto run_setup = [&]() -> int {
+    int s2 = reset_device_flags(c);
+    if (s2) return s2;
+    s2 = tsf::launch_setup(A, c->grid, c->smem, c->stream, c->omega, (double2 *)A.What, (double2 *)A.LamW,
+                           (double2 *)A.LamQ, (double2 *)A.BhI, c->BhF, (double2 *)A.chirpI,
+                           (double2 *)A.twL, c->beta, A.precond);
+    if (s2) return s2;
+    CK(cudaStreamSynchronize(c->stream));
+    int d2 = 0;
+    s2 = device_status(c, &d2);
+    return s2 ? s2 : d2;
+  };
+  st = run_setup();
   if (st) return st;
-  st = tsf::launch_setup(A, c->grid, c->smem, c->stream, c->omega, (double2 *)A.What, (double2 *)A.LamW,
-                         (double2 *)A.LamQ, (double2 *)A.BhI, c->BhF, (double2 *)A.chirpI,
-                         (double2 *)A.twL, c->beta, A.precond);
-  if (st) return st;
-  CK(cudaStreamSynchronize(c->stream));
-  int dst = 0;
-  st = device_status(c, &dst);
-  if (st) return st;
-  if (dst) return dst;
+  if (c->opt.autotune) {
+    // time y = A x of level 0 (symbols and one Toeplitz product, the march's passes) for each
+    // candidate split and chunk budget; keep the fastest
+    const int lg0 = A.cp.lgN / 2;
+    int best_lg1 = A.cp.lg1, best_budget = c->budget;
+    float best = 1e30f;
+    for (int d = -1; d <= 1; ++d) {
+      const int lg1 = lg0 + d;
+      if (lg1 < 1 || A.cp.lgN - lg1 < 1) continue;
+      for (int budget : {2048, 4096}) {
+        set_split(A, lg1);
+        set_caps(A, c->grid, budget);
+        c->smem = tsf::level_smem_bytes(A);
+        if (c->smem > smem_limit) continue;
+        st = run_setup();
+        if (st) return st;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          st = reset_device_flags(c);
+          if (st) return st;
+          CK(cudaEventRecord(c->ev0, c->stream));
+          st = tsf::launch_apply(A, c->grid, c->smem, c->stream, 0, 0, A.vh, A.H);
+          if (st) return st;
+          CK(cudaEventRecord(c->ev1, c->stream));
+          CK(cudaStreamSynchronize(c->stream));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+          if (rep) tot += ms;
+        }
+        if (tot < best) {
+          best = tot;
+          best_lg1 = lg1;
+          best_budget = budget;
+        }
+      }
+    }
+    set_split(A, best_lg1);
+    c->budget = best_budget;
+    set_caps(A, c->grid, c->budget);
+    c->smem = tsf::level_smem_bytes(A);
+    c->tune_best_us = 1e3 * best / 3.0;
+    st = run_setup();
+    if (st) return st;
+  }
   c->level = 0;
   return TSFCDE_OK;
 }
@@ -577,6 +643,28 @@ int tsfcde_apply(tsfcde_ctx *c, int32_t op, int64_t j, const double *x, double *
   st = device_status(c, &dst);
   if (st) return st;
   return dst;
+}
+
+int tsfcde_get_plan(tsfcde_ctx *c, int32_t *N1, int32_t *N2, int32_t *budget, double *best_us) {
+  if (!c) return TSFCDE_E_INVALID_ARG;
+  if (N1) *N1 = c->A.cp.N1;
+  if (N2) *N2 = c->A.cp.N2;
+  if (budget) *budget = c->budget;
+  if (best_us) *best_us = c->tune_best_us;
+  return TSFCDE_OK;
+}
+
+int tsfcde_history_sum(tsfcde_ctx *c, int64_t j, double *H_out) {
+  if (!c || j < 1 || j > c->level) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  int st = reset_device_flags(c);
+  if (st) return st;
+  // H is rewritten by every level before use, so it serves as the output here
+  st = tsf::launch_history(c->A, c->grid, c->smem, c->stream, (int)j);
+  if (st) return st;
+  if (H_out) CK(cudaMemcpyAsync(H_out, c->A.H, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return TSFCDE_OK;
 }
 
 }  // extern "C"

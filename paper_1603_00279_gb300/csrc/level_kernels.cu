@@ -868,6 +868,14 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
 }
 
 // ------------------------------------------------------------------------------------------------
+// diagnostic: the history sum of level j alone (the march's phase, no commit)
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) history_kernel(Args A, int j) {
+  grid_sync_init();
+  ph_history(A, j, false);
+}
+
+// ------------------------------------------------------------------------------------------------
 // diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}); x and y are padded device vectors.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int j, const double *xin, double *yout) {
@@ -1192,6 +1200,13 @@ size_t level_smem_bytes(const Args &A) {
 }
 
 const void *level_kernel_ptr() { return (const void *)level_kernel; }
+const void *history_kernel_ptr() { return (const void *)history_kernel; }
+
+int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j) {
+  Args a = A;
+  void *args[] = {&a, &j};
+  return coop_launch((const void *)history_kernel, grid, smem, st, args);
+}
 const void *batch_level_kernel_ptr() { return (const void *)batch_level_kernel; }
 const void *batch_setup_kernel_ptr() { return (const void *)batch_setup_kernel; }
 

@@ -140,3 +140,38 @@ def test_large_config_proxy_first_levels():
         got = s.get_level()[0]
         assert rel_l2(got, ref[j + 1]) <= 1e-10, (j, rel_l2(got, ref[j + 1]))
     s.close()
+
+
+def test_history_sum_matches_lemma1():
+    """The march's history phase (Lemma 1's sum over all earlier increments) for level j equals
+    sum_{s<j} c^{(j)}_{j-s} (u^{s+1} - u^s) evaluated on the host from the same levels."""
+    P = solver_module()
+    prob = W.config_small(n=255, M=24)
+    s = P.Solver.from_problem(prob)
+    levels = [s.get_level()[0]]
+    for _ in range(prob.M):
+        s.step(1)
+        levels.append(s.get_level()[0])
+    for j in (1, 2, 7, 23):
+        c = O.c_coeffs(prob.alpha, j)
+        ref = sum(c[j - k] * (levels[k + 1] - levels[k]) for k in range(j))
+        got = s.history_sum(j)
+        assert np.linalg.norm(got - ref) <= 1e-13 * max(1e-300, np.linalg.norm(ref)) + 1e-18
+    s.close()
+
+
+@pytest.mark.parametrize("n", [127, 4095])
+def test_autotuned_plan_matches_oracle(n):
+    """The setup-time autotuner picks one of the candidate FFT splits and chunk sizes; the march
+    with that plan still matches the oracle at every level."""
+    P = solver_module()
+    prob = W.config_small(n=n, M=6)
+    s = P.Solver.from_problem(prob, autotune=True)
+    plan = s.plan()
+    N = max(8, 1 << int(np.ceil(np.log2(2 * n)))) // 2
+    assert plan["N1"] * plan["N2"] == N and plan["budget"] in (2048, 4096) and plan["best_us"] > 0
+    ref = O.run(prob)
+    for j in range(prob.M):
+        s.step(1)
+        assert rel_l2(s.get_level()[0], ref[j + 1]) <= 1e-10
+    s.close()
