@@ -70,7 +70,9 @@ def workload(name: str, precond):
     elif name == "mixed":
         p = W.config_mixed()
     elif name == "batch":
-        return W.config_batch(count=_ARGS.instances)
+        return W.config_batch(count=_ARGS.instances or 4096)
+    elif name == "history":
+        return W.config_history()[:(_ARGS.instances or 1)]
     else:
         raise SystemExit(f"unknown workload {name}")
     if precond:
@@ -488,6 +490,87 @@ def run_native_batch(args, probs):
     print(json.dumps(line))
 
 
+def run_native_history(args, probs):
+    """History-dominated workload: instances of n = 2^18-1, M = 8192 marched one after another
+    (each holds a 17 GB FP64 history), FP64 history accumulation, the given precision for the
+    solves."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1603_00279_gb300 import build
+    build.build()
+    import paper_1603_00279_gb300 as P
+    stream = torch.cuda.Stream()
+    ntot = sum(q.n * q.M for q in probs)
+    ctxs = [P.Solver.from_problem(q, source="separable", stream=stream.cuda_stream,
+                                  precision=args.precision, maxit=args.maxit) for q in probs]
+
+    def one_step():
+        out = []
+        for q, s in zip(probs, ctxs):
+            s.reset()
+            out.append(s.step(q.M))
+        return out
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        stats = [one_step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # history phase at the last level of the first instance
+    q0, s0 = probs[0], ctxs[0]
+    jh = q0.M - 1
+    s0.history_sum(jh, want=False)
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(3):
+        s0.history_sum(jh, want=False)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    hms = h0.elapsed_time(h1) / 3
+    hbytes = 8.0 * q0.n * jh + 16.0 * q0.n
+    peak = hbm_peak()
+    errs = []
+    for q, s in zip(probs, ctxs):
+        u, _ = s.get_level()
+        errs.append(float(np.sqrt(q.h) * np.linalg.norm(u - q.exact(q.grid(), q.T))))
+    co = None
+    if args.co:
+        q = probs[0]
+        half = W.config_history()[0]
+        half.M = q.M // 2
+        with P.Solver.from_problem(half, source="separable", precision=args.precision) as sh:
+            uh = sh.solve()
+        eh = float(np.sqrt(half.h) * np.linalg.norm(uh - half.exact(half.grid(), half.T)))
+        co = {"E_M/2": eh, "E_M": errs[0], "CO_tau": math.log2(eh / errs[0])}
+    for s in ctxs:
+        s.close()
+    its = [st["total_iterations"] / max(1, st["levels_advanced"]) for step in stats for st in step]
+    line = {"metric": "grid-point updates/s", "value": ntot * args.steps / (ms / 1e3),
+            "unit": "updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32/ff inner / f64 refinement, f64 history",
+            "data": "synthetic (manufactured solution)",
+            "config": {"workload": "tsfcde_history", "instances": len(probs), "n": probs[0].n,
+                       "M": probs[0].M, "alpha_beta": [[q.alpha, q.beta] for q in probs],
+                       "history_bytes_per_instance": 8 * probs[0].n * probs[0].M},
+            "history_roofline": {"kernel": "history phase (level M-1)", "bound": "hbm",
+                                 "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak[0],
+                                 "unit": "GB/s", "frac": hbytes / (hms / 1e3) / 1e9 / peak[0],
+                                 "ms": hms, "fp64_tflops": 2.0 * q0.n * jh / (hms / 1e3) / 1e12,
+                                 "peak_source": peak[1]},
+            "cgs_iterations_mean": float(np.mean(its)), "l2_error_vs_exact_at_T": errs,
+            "convergence_order": co, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,16 +585,25 @@ def main():
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--instances", type=int, default=4096, help="batch workload: instance count")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batch workload: instance count (4096); history workload: how many of "
+                         "its 16 instances to march (1)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the setup-time FFT-plan tuner")
+    ap.add_argument("--co", action="store_true", help="history workload: also run M/2 for CO_tau")
     args = ap.parse_args()
     global _ARGS
     _ARGS = args
     p = workload(args.workload, args.precond)
     if args.precision is None:
         args.precision = "mixed" if args.workload == "mixed" else "fp64"
-    if args.levels and args.workload != "batch":
+    if args.levels and args.workload not in ("batch", "history"):
         p.M = args.levels
+    if args.levels and args.workload == "history":
+        for q in p:
+            q.M = args.levels
+    if args.workload == "history":
+        run_native_history(args, p)
+        return
     if args.workload == "batch":
         if args.levels:
             for q in p:

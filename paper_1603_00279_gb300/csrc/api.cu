@@ -329,6 +329,8 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
       A.Y1f = cv.take<float2>(N);
       A.Y2f = cv.take<float2>(N);
       A.twL32 = cv.take<float2>(Lp);
+      A.x32b = cv.take<float>(Lp);
+      A.xffb = cv.take<tsf::ff>(Lp);
       A.xff = cv.take<tsf::ff>(Lp);
       A.rff = cv.take<tsf::ff>(Lp);
       A.rtff = cv.take<tsf::ff>(Lp);

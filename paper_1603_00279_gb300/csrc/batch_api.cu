@@ -251,6 +251,8 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
         C.SP32 = cs.take<float2>(Nmax + 1);
         C.Y1f = cs.take<float2>(Nmax);
         C.Y2f = cs.take<float2>(Nmax);
+        C.x32b = cs.take<float>(Lmax);
+        C.xffb = cs.take<tsf::ff>(Lmax);
         C.xff = cs.take<tsf::ff>(Lmax);
         C.rff = cs.take<tsf::ff>(Lmax);
         C.rtff = cs.take<tsf::ff>(Lmax);

@@ -516,17 +516,23 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
   rel = 0.0;
   alive = true;
   if (!(nref > 0.0)) return kOK;
+  // the start x0 (zero when fwd_done) is the first candidate for the minimum-residual iterate
+  bool have = false;       // xb holds a saved iterate (else the best is x0 = 0)
   if (!fwd_done) {
+    const bool keep0 = V.xb != nullptr;
     col_pass<false, true, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, V.Y1,
-                             [&](int m, T) -> T { return ldp<T>(V.p, m); });
+                             [&](int m, T) -> T {
+                               if (keep0) stp<T>(V.xb, m, ldp<T>(V.x, m));
+                               return ldp<T>(V.p, m);
+                             });
+    have = keep0;
     if (!(alive = grid_sync(A))) return kOK;
   }
   double tot[3];
   bool first = true;
   double beta = 0.0;
-  double best = 1.0;       // smallest ||r_k|| / nref so far (the start has 1 when x0 = 0)
+  double best = sqrt(rho) / nref;   // ||r_0|| / nref (r~ = r at the start, so rho = ||r_0||^2)
   bool save = false;       // the iterate after the last iteration is the best so far
-  bool have = false;       // a best iterate has been copied to xb
   while (true) {
     ++its;
     if (!first) {
@@ -645,10 +651,18 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
     if (save) best = rel;
     if (its >= maxit) {
       // like MATLAB's cgs: a solve that does not converge returns its minimum-residual iterate
-      if (V.xb != nullptr && !save && have) {
+      // (the saved one, or the zero start when nothing improved on it)
+      if (V.xb != nullptr && !save) {
+        const bool from_xb = have;
         col_pass<false, false, T>(A, S, V.twG, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, nullptr,
                                   [&](int m, T z) -> T {
-                                    stp<T>(V.x, m, ldp<T>(V.xb, m));
+                                    T v;
+                                    if (from_xb) {
+                                      v = ldp<T>(V.xb, m);
+                                    } else {
+                                      mkc(v, (R)0, (R)0);
+                                    }
+                                    stp<T>(V.x, m, v);
                                     return z;
                                   });
         if (!(alive = grid_sync(A))) return kOK;
@@ -708,11 +722,11 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   V64.SA = A.SA; V64.SP = A.SP; V64.Y1 = A.Y1; V64.Y2 = A.Y2; V64.twG = A.twL;
   Krylov<float2> V32;
   V32.x = A.x32; V32.r = A.r32; V32.rt = A.rt32; V32.p = A.p32; V32.q = A.q32; V32.uu = A.uu32;
-  V32.xb = nullptr;
+  V32.xb = A.x32b;
   V32.vh = A.vh32; V32.SA = A.SA32; V32.SP = A.SP32; V32.Y1 = A.Y1f; V32.Y2 = A.Y2f; V32.twG = A.twL32;
   Krylov<ffc> VF;
   VF.x = A.xff; VF.r = A.rff; VF.rt = A.rtff; VF.p = A.pff; VF.q = A.qff; VF.uu = A.uuff;
-  VF.xb = nullptr;
+  VF.xb = A.xffb;
   VF.vh = A.vhff; VF.SA = A.SAff; VF.SP = A.SPff; VF.Y1 = A.Y1ff; VF.Y2 = A.Y2ff; VF.twG = A.twLff;
 
   for (int j = j0; j < j1; ++j) {
@@ -1008,6 +1022,7 @@ __device__ __forceinline__ void patch_cta_scratch(Args &A, const CtaScratch &C) 
   A.uu32 = C.uu32; A.vh32 = C.vh32; A.SA32 = C.SA32; A.SP32 = C.SP32; A.Y1f = C.Y1f; A.Y2f = C.Y2f;
   A.xff = C.xff; A.rff = C.rff; A.rtff = C.rtff; A.pff = C.pff; A.qff = C.qff; A.uuff = C.uuff;
   A.vhff = C.vhff; A.SAff = C.SAff; A.SPff = C.SPff; A.Y1ff = C.Y1ff; A.Y2ff = C.Y2ff;
+  A.x32b = C.x32b; A.xffb = C.xffb;
 }
 
 // One instance's weights (Lemma 2) and level tables (Lemma 1) with a one-CTA team; constant

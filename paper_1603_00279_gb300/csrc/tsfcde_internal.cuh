@@ -82,6 +82,7 @@ struct Args {
   int inner_maxit, outer_maxit;
   double *g;              // FP64 right-hand side of the level
   float *x32, *r32, *rt32, *p32, *q32, *uu32, *vh32;   // FP32 inner Krylov vectors (L each)
+  float *x32b;            // minimum-residual iterate of the FP32 inner solve
   float2 *SA32, *SP32;    // FP32 copies of the level spectra (rounded from FP64)
   float2 *Y1f, *Y2f;      // FP32 FFT work, L/2 complex each
   float2 *twL32;          // FP32 twiddles (rounded from the FP64 table)
@@ -93,6 +94,7 @@ struct Args {
   const int *lv_inner;    // per level: 0 FP32 inner solve, 1 float-float inner solve
   const double *lv_floor; // per level: FP64 residual accepted once refinement stagnates below it
   ff *xff, *rff, *rtff, *pff, *qff, *uuff, *vhff;   // float-float Krylov vectors (L each)
+  ff *xffb;               // minimum-residual iterate of the float-float inner solve
   ffc *SAff, *SPff;       // float-float spectra (rounded from FP64), N+1
   ffc *Y1ff, *Y2ff;       // float-float FFT work, L/2 each
   ffc *twLff;             // float-float twiddles, L
@@ -437,6 +439,8 @@ struct CtaScratch {
   float2 *SA32, *SP32, *Y1f, *Y2f;
   ff *xff, *rff, *rtff, *pff, *qff, *uuff, *vhff;
   ffc *SAff, *SPff, *Y1ff, *Y2ff;
+  float *x32b;
+  ff *xffb;
 };
 // Per-instance inputs of the batched setup (constant coefficients).
 struct InstanceSetup {

@@ -50,13 +50,13 @@ def test_mixed_matches_fp64_gpu_path():
 
 
 def test_mixed_escalates_when_fp32_cannot_converge():
-    """beta = 1.9, alpha = 0.3 at n = 4095 with the inner solve forced to FP32: u32 * kappa_eff
-    ~ 0.3, FP32 cannot make progress; such levels must be finished by the FP64 CGS and still
-    match FP64."""
+    """beta = 1.9, alpha = 0.3 at n = 4095 with the inner solve forced to FP32 (u32 * kappa_eff
+    ~ 0.3: each refinement step gains little) and one refinement step allowed: the levels must be
+    finished by the FP64 CGS from the current iterate and still match FP64."""
     P = solver_module()
     prob = W.config_large(n=4095, M=1024, preconditioner="strang")
     a, _ = _levels(P, prob, 6, precision="fp64")
-    b, st = _levels(P, prob, 6, precision="mixed", inner="fp32")
+    b, st = _levels(P, prob, 6, precision="mixed", inner="fp32", outer_maxit=1)
     assert max(rel_l2(b[j], a[j]) for j in range(7)) <= 1e-8
     assert sum(s["escalated_levels"] for s in st) >= 1
 
@@ -80,3 +80,15 @@ def test_float_float_small_config_every_level():
     got, st = _levels(P, prob, prob.M, precision="mixed", inner="ff")
     assert max(rel_l2(got[j], ref[j]) for j in range(prob.M + 1)) <= 1e-8
     assert sum(s["escalated_levels"] for s in st) == 0
+
+
+def test_mixed_tchan_large_never_worse_than_fp64():
+    """T. Chan at n = 65535 (hundreds of CGS iterations per solve, irregular convergence): inner
+    solves that fail to converge return their minimum-residual iterate, so no refinement step can
+    make x worse; every level must still match the FP64 path to 1e-8."""
+    P = solver_module()
+    prob = W.config_large(n=65535, M=1024, preconditioner="tchan")
+    a, _ = _levels(P, prob, 6, precision="fp64")
+    b, st = _levels(P, prob, 6, precision="mixed")
+    assert max(rel_l2(b[j], a[j]) for j in range(7)) <= 1e-8
+    assert max(s["max_residual"] for s in st) < 1e-6
