@@ -39,6 +39,7 @@ struct tsfcde_ctx {
   std::vector<double> lv_floor;
   int budget = 4096;
   double tune_best_us = 0.0;
+  int march_grid = 0;   // CTAs of the level-march launch (1: one-CTA team for small N)
 };
 
 namespace {
@@ -101,6 +102,13 @@ void set_split(Args &A, int lg1) {
   A.cp.N1 = 1 << A.cp.lg1;
   A.cp.N2 = 1 << A.cp.lg2;
 }
+
+// Largest FFT half-length N whose march runs in one CTA (block barriers only): below it the
+// grid barriers of a whole-GPU launch cost more than the work they spread.
+#ifndef TSFCDE_CTA_MARCH_MAX_N
+#define TSFCDE_CTA_MARCH_MAX_N 256
+#endif
+constexpr int kCtaMarchMaxN = TSFCDE_CTA_MARCH_MAX_N;
 
 // Lines per CTA chunk in each pass kind for a grid of G CTAs and a per-buffer budget.
 void set_caps(Args &A, int G, int budget) {
@@ -256,6 +264,16 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
       if (occ < 1) return TSFCDE_E_INVALID_ARG;
     }
+  }
+
+  // ---- small instances: the march runs in one CTA (level_kernel_cta) ----
+  c->march_grid = (A.cp.N <= kCtaMarchMaxN) ? 1 : c->grid;
+  if (c->march_grid == 1) {
+    Args B = A;
+    set_caps(B, 1, c->budget);
+    const size_t sm1 = tsf::level_smem_bytes(B);
+    CK(cudaFuncSetAttribute(tsf::level_kernel_cta_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)std::max(sm1, c->smem)));
   }
 
   // ---- device memory: one arena + the history ring ----
@@ -538,7 +556,13 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     int st = reset_device_flags(c);
     if (st) return st;
     CK(cudaEventRecord(c->ev0, c->stream));
-    st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
+    if (c->march_grid == 1) {
+      Args B = c->A;   // one-CTA team: every pass item belongs to the single CTA
+      set_caps(B, 1, c->budget);
+      st = tsf::launch_levels(B, 1, tsf::level_smem_bytes(B), c->stream, (int)s, (int)e);
+    } else {
+      st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
+    }
     c->A.test_skip = 0;   // the testing hook applies to one launch only
     if (st) return st;
     CK(cudaEventRecord(c->ev1, c->stream));

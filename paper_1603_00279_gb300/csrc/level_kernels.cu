@@ -881,6 +881,13 @@ __global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int 
   march_body(A, S, j0, j1);
 }
 
+// Small instances: the same march by one CTA with block barriers only (no grid barrier cost).
+__global__ void __launch_bounds__(kThreads, 1) level_kernel_cta(Args A, int j0, int j1) {
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
+  cta_team_init();
+  march_body(A, S, j0, j1);
+}
+
 // ------------------------------------------------------------------------------------------------
 // diagnostic: the history sum of level j alone (the march's phase, no commit)
 // ------------------------------------------------------------------------------------------------
@@ -1237,9 +1244,14 @@ const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
 
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1) {
   Args a = A;
+  if (grid == 1) {   // one-CTA team
+    level_kernel_cta<<<1, kThreads, smem, st>>>(a, j0, j1);
+    return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+  }
   void *args[] = {&a, &j0, &j1};
   return coop_launch((const void *)level_kernel, grid, smem, st, args);
 }
+const void *level_kernel_cta_ptr() { return (const void *)level_kernel_cta; }
 
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
                  const double *xin, double *yout) {

@@ -470,6 +470,7 @@ int launch_time_tables(int M, double alpha, double tau, double h, double beta, c
                        double *q, double *kp, double *km, cudaStream_t st);
 size_t level_smem_bytes(const Args &A);
 const void *level_kernel_ptr();
+const void *level_kernel_cta_ptr();
 const void *history_kernel_ptr();
 int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j);
 const void *batch_level_kernel_ptr();

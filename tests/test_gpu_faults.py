@@ -13,9 +13,11 @@ pytestmark = pytest.mark.gpu
 def test_barrier_wait_times_out_and_context_recovers():
     """CTA 0 skips its first grid-barrier arrival (testing hook, one launch only); every other
     CTA's wait runs into its bound (2^16 polls) and the call returns E_TIMEOUT.  The same
-    context then resets and marches normally, matching the oracle."""
+    context then resets and marches normally, matching the oracle.  n=511 (FFT half-length 512)
+    so that the march runs on the whole grid: up to half-length 256 it runs in one CTA, which
+    has no grid barrier."""
     P = solver_module()
-    prob = W.config_small(M=6)
+    prob = W.config_small(n=511, M=6)
     s = P.Solver.from_problem(prob, barrier_spin_log2=16, test_skip_arrival=True)
     with pytest.raises(P.TsfcdeError) as e:
         s.step(1)
