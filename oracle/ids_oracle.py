@@ -14,6 +14,12 @@ preconditioners (Eq. (3.7), Strang and T. Chan) and a dense preconditioned CGS a
 out densely, but only so that tests can pin iteration counts and preconditioner definitions; they
 do not feed the level solutions.
 
+For constant coefficients (Section 3.2) `run_const` follows Algorithm "Practical implementation of
+IDS with constant coefficients": level 0 by elimination, every later level by the Gohberg-Semencul
+formula (after Eq. (3.4)) applied as in Algorithm "Compute z = A^{-1} v", with the two generator
+systems of Eq. (3.4) solved by elimination and the four triangular Toeplitz factors formed densely.
+It reaches the same level solutions as `run` up to rounding, which the tests check.
+
 Notation follows the paper except that n = N - 1 is the number of interior unknowns,
 h = (b - a) / (n + 1), tau = T / M, sigma = 1 - alpha/2.
 
@@ -165,13 +171,15 @@ def level_matrices(prob, j: int, Q=None, W=None):
 # ----------------------------------------------------------------------------------------------
 
 
-def run(prob, levels: Optional[int] = None, source: Optional[Callable] = None) -> List[np.ndarray]:
+def run(prob, levels: Optional[int] = None, source: Optional[Callable] = None,
+        solve: Optional[Callable] = None) -> List[np.ndarray]:
     """Return [u^0, u^1, ..., u^levels] (interior values) for the problem `prob`.
 
     For j = 0..levels-1 (Eq. (3.1)):
         g = B^{(j+sigma)} u^j - tau^{-alpha}/Gamma(2-alpha) sum_{s<j} c^{(j)}_{j-s} (u^{s+1}-u^s)
             + f(x, t_{j+sigma})
         A^{(j+sigma)} u^{j+1} = g        (Gaussian elimination with partial pivoting)
+    `solve(j, A, g)` replaces the elimination when given (see run_const).
     """
     M = prob.M if levels is None else levels
     n = prob.n
@@ -194,8 +202,86 @@ def run(prob, levels: Optional[int] = None, source: Optional[Callable] = None) -
             g = g - hist_scale * H
         if f is not None:
             g = g + f(x, (j + sigma) * tau)
-        u.append(np.linalg.solve(A, g))
+        u.append(np.linalg.solve(A, g) if solve is None else solve(j, A, g))
     return u
+
+
+# ----------------------------------------------------------------------------------------------
+# Constant coefficients (Section 3.2): the Gohberg-Semencul formula after Eq. (3.4), Algorithm
+# "Compute z = A^{-1} v" and Algorithm "Practical implementation of IDS with constant
+# coefficients".  Dense matrices throughout; no FFT.
+# ----------------------------------------------------------------------------------------------
+
+
+def gs_generators(A: np.ndarray):
+    """x = A^{-1} e_1 and y = A^{-1} e_n, the two systems of Eq. (3.4), by Gaussian elimination."""
+    n = A.shape[0]
+    E = np.zeros((n, 2))
+    E[0, 0] = 1.0
+    E[n - 1, 1] = 1.0
+    X = np.linalg.solve(A, E)
+    return X[:, 0].copy(), X[:, 1].copy()
+
+
+def gs_factors(x, y):
+    """The four triangular Toeplitz matrices of the Gohberg-Semencul formula, entry by entry
+    (generic element type, so exact rationals work):
+        L_p [i,k] = xi_{i-k}          (i >= k)   lower, first column x
+        R_p [i,k] = eta_{n-1-(k-i)}   (k >= i)   upper, first row (eta_{n-1}, ..., eta_0)
+        L0_p[i,k] = eta_{i-k-1}       (i >  k)   strictly lower, first column (0, eta_0, ...)
+        R0_p[i,k] = xi_{n-(k-i)}      (k >  i)   strictly upper, first row (0, xi_{n-1}, ..., xi_1)
+    Returned as lists of rows."""
+    n = len(x)
+    zero = x[0] - x[0]
+    Lp = [[x[i - k] if i >= k else zero for k in range(n)] for i in range(n)]
+    Rp = [[y[n - 1 - (k - i)] if k >= i else zero for k in range(n)] for i in range(n)]
+    L0 = [[y[i - k - 1] if i > k else zero for k in range(n)] for i in range(n)]
+    R0 = [[x[n - (k - i)] if k > i else zero for k in range(n)] for i in range(n)]
+    return Lp, Rp, L0, R0
+
+
+def _matmul_rows(P, Q):
+    n = len(P)
+    return [[sum((P[i][m] * Q[m][k] for m in range(n)), P[0][0] - P[0][0]) for k in range(n)]
+            for i in range(n)]
+
+
+def gs_inverse(x, y):
+    """A^{-1} = (L_p R_p - L0_p R0_p) / xi_0 (Gohberg-Semencul formula; requires xi_0 != 0).
+    Plain loops over entries: for pins on small n, any element type with + - * /."""
+    Lp, Rp, L0, R0 = gs_factors(x, y)
+    P1 = _matmul_rows(Lp, Rp)
+    P2 = _matmul_rows(L0, R0)
+    n = len(x)
+    return [[(P1[i][k] - P2[i][k]) / x[0] for k in range(n)] for i in range(n)]
+
+
+def gs_apply(x: np.ndarray, y: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Algorithm "Compute z = A^{-1} v": z1 = R0_p v, z2 = R_p v, z3 = L0_p z1, z4 = L_p z2,
+    z = (z4 - z3) / xi_0, with the triangular Toeplitz matrices formed densely (FP64)."""
+    Lp, Rp, L0, R0 = (np.array(F, dtype=np.float64) for F in gs_factors(list(x), list(y)))
+    z1 = R0 @ v
+    z2 = Rp @ v
+    z3 = L0 @ z1
+    z4 = Lp @ z2
+    return (z4 - z3) / x[0]
+
+
+def run_const(prob, levels: Optional[int] = None, source: Optional[Callable] = None) -> List[np.ndarray]:
+    """Algorithm "Practical implementation of IDS with constant coefficients": level 0 solves
+    A^{(sigma)} u^1 = g^1 by elimination; every later level, whose matrix A is the same for
+    j = 1..M-1 when gamma and d_+- are constant (Eq. (3.4) context), computes u^{j+1} = A^{-1} g
+    by Algorithm "Compute z = A^{-1} v" with the generators of that A."""
+    gen = {}
+
+    def solve(j, A, g):
+        if j == 0:
+            return np.linalg.solve(A, g)
+        if "xy" not in gen:
+            gen["xy"] = gs_generators(A)
+        return gs_apply(gen["xy"][0], gen["xy"][1], g)
+
+    return run(prob, levels, source, solve)
 
 
 def l2_norm(v: np.ndarray, h: float) -> float:
