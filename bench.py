@@ -106,6 +106,22 @@ def _alg_flops(n, M, preconditioner, iters, newsym_levels):
     return conv * convs + sym * newsym_levels + hist + vec
 
 
+def _alg_flops_const(n, M, preconditioner, iters, applications):
+    """Algorithm "... with constant coefficients": the CGS iterations of level 0 and of the two
+    generator solves, one right-hand-side product per level, and per application of A^{-1}
+    four triangular Toeplitz products plus the FP64 residual product; the generator refinement
+    (2 x 5 products) and the factor spectra (8 forward transforms, once per march)."""
+    L = max(8, 1 << math.ceil(math.log2(2 * n)))
+    lg = math.log2(L)
+    conv = 5.0 * L * lg + 3.0 * L
+    pc = preconditioner != "none"
+    convs = M + (4 if pc else 2) * float(iters.sum()) + 5.0 * applications + 10.0 + 4.0
+    sym = (12.5 * L * lg + 24.0 * n) if pc else 0.0
+    hist = 2.0 * n * (M * (M - 1) / 2.0)
+    vec = 19.0 * n * float(iters.sum()) + 12.0 * n * M + 6.0 * n * applications
+    return conv * convs + sym * 2 + hist + vec
+
+
 # ---------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -403,8 +419,9 @@ def run_native_batch(args, probs):
     M = probs[0].M
     precond = args.precond or "strang"
     stream = torch.cuda.Stream()
+    const = args.algorithm == "ids-const"
     b = P.Batch(probs, M, preconditioner=precond, precision=args.precision,
-                maxit=args.maxit, stream=stream.cuda_stream)
+                maxit=args.maxit, stream=stream.cuda_stream, algorithm=args.algorithm)
     ntot = sum(p.n for p in probs)
 
     def one_step():
@@ -428,10 +445,14 @@ def run_native_batch(args, probs):
     kernel_ms = float(np.mean([st["device_ms"] for st in stats]))
     flops = 0.0
     its_all = []
+    apps_per_level = (stats[-1]["outer_iterations"] / max(1, stats[-1]["gsf_levels"])) if const else 0.0
     for i, p in enumerate(probs):
         it, _ = b.history(i, M)
         its_all.append(it)
-        flops += _alg_flops(p.n, M, precond, it, 2)
+        if const:
+            flops += _alg_flops_const(p.n, M, precond, it, apps_per_level * (M - 1))
+        else:
+            flops += _alg_flops(p.n, M, precond, it, 2)
     its_all = np.concatenate(its_all)
     # end to end: H2D of every u^0, march, D2H of every u^M through the C ABI
     u0 = torch.from_numpy(np.concatenate([np.asarray(p.phi(p.grid()), dtype=np.float64)
@@ -456,6 +477,8 @@ def run_native_batch(args, probs):
         "config": {"workload": "tsfcde_batch", "instances": len(probs), "M": M,
                    "n_min": int(ns.min()), "n_max": int(ns.max()), "sum_n": int(ntot),
                    "preconditioner": precond, "tol": 1e-12, "parallelism": "replicas1",
+                   "algorithm": ("IDS with constant coefficients (Gohberg-Semencul, levels >= 1)"
+                                 if const else "IDS (PCGS every level)"),
                    "updates_per_step": int(ntot * M),
                    "l2": "inputs larger than L2 (history %.1f GB)" % (ntot * M * 8 / 1e9)},
         "e2e": {"value": ntot * M / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": 8 * int(ntot),
@@ -468,7 +491,11 @@ def run_native_batch(args, probs):
         "max_level_residual": float(max(st["max_residual"] for st in stats)),
         "refinement": ({"outer_steps": int(stats[-1]["outer_iterations"]),
                         "escalated_levels": int(stats[-1]["escalated_levels"])}
-                       if args.precision == "mixed" else None),
+                       if args.precision == "mixed" and not const else None),
+        "gohberg_semencul": ({"levels": int(stats[-1]["gsf_levels"]),
+                              "applications_per_level": apps_per_level,
+                              "note": "cgs_iterations include the two generator solves at level 1"}
+                             if const else None),
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
@@ -589,6 +616,8 @@ def main():
                     help="batch workload: instance count (4096); history workload: how many of "
                          "its 16 instances to march (1)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the setup-time FFT-plan tuner")
+    ap.add_argument("--algorithm", default="ids", choices=["ids", "ids-const"],
+                    help="batch workload: ids-const = constant-coefficient algorithm (Gohberg-Semencul)")
     ap.add_argument("--co", action="store_true", help="history workload: also run M/2 for CO_tau")
     args = ap.parse_args()
     global _ARGS

@@ -92,7 +92,26 @@ typedef struct tsfcde_options {
                                 N2/2, N2, 2 N2) and per-pass chunk sizes on the level operator
                                 product and keep the fastest (see tsfcde_get_plan); 0: default
                                 plan (N1 <= N2, N1 >= N2/2, chunks of 4096 values)            */
+  int32_t algorithm;         /* TSFCDE_ALG_IDS (default) or TSFCDE_ALG_IDS_CONST, below        */
 } tsfcde_options;
+
+/* Level algorithm.
+ * TSFCDE_ALG_IDS: Algorithm "Practical implementation of IDS" -- every level solved by the
+ *   circulant-preconditioned CGS.
+ * TSFCDE_ALG_IDS_CONST: Algorithm "Practical implementation of IDS with constant coefficients"
+ *   (Section 3.2), for gamma, d_+ and d_- constant in t.  Then A^{(j+sigma)} = A for every
+ *   j >= 1 (Eq. (3.4) context).  Level 0 is solved by CGS as usual.  At level 1 the two systems
+ *   A x = e_1 and A y = e_N of Eq. (3.4) are solved by the preconditioned CGS, each refined once
+ *   with the inverse they define.  Every level j >= 1 then computes u^{j+1} = A^{-1} g by the
+ *   Gohberg-Semencul formula: Algorithm "Compute z = A^{-1} v", four triangular Toeplitz products
+ *   by FFT, with no Krylov iterations.  The level's FP64 residual ||g - A u^{j+1}|| / ||g|| is
+ *   measured.  While it is above both tol and 64 u64 kappa_eff, the level is refined,
+ *   u += A^{-1}(g - A u), at most twice.  A level still above both is reported as
+ *   TSFCDE_E_NOT_CONVERGED with its state kept.
+ *   tsfcde_setup returns TSFCDE_E_INVALID_ARG if gamma, d_+ or d_- differ between two levels
+ *   j, j' >= 1; it returns TSFCDE_E_BREAKDOWN from the step if xi_0 = (A^{-1})_{11} is zero. */
+#define TSFCDE_ALG_IDS 0
+#define TSFCDE_ALG_IDS_CONST 1
 
 /* Inner precision of TSFCDE_MIXED.  AUTO estimates per level kappa_eff = max|A^| / eta_j <=
  * 1 + sigma ((kappa_+ + kappa_-) 2|omega_1| + 2|q|) / eta_j (Remark 3.1 bounds the eigenvalues
@@ -120,7 +139,9 @@ typedef struct tsfcde_stats {
   double device_ms;         /* device time of those launches (CUDA events on their stream)  */
   int64_t outer_iterations; /* MIXED: refinement steps summed over the levels advanced      */
   int32_t escalated_levels; /* MIXED: levels finished by the float64 CGS                    */
-  int32_t pad_;
+  int32_t gsf_levels;       /* IDS_CONST: levels solved by the Gohberg-Semencul formula; for
+                               these, iterations count the two generator solves (level 1 only)
+                               and outer_iterations the applications of A^{-1} (1 + refinements) */
 } tsfcde_stats;
 
 /* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */
@@ -173,10 +194,13 @@ int tsfcde_get_history(tsfcde_ctx *ctx, int32_t *iters, double *resid, int64_t c
 
 /* Diagnostic products with the level-j operators (Eq. (3.3), Eq. (3.7)), computed by the same
  * device kernels as the march: op = 0: y = A^{(j+sigma)} x, 1: y = B^{(j+sigma)} x,
- * 2: y = (P^{(j+sigma)})^{-1} x.  x, y: N host values.  Does not change the march state. */
+ * 2: y = (P^{(j+sigma)})^{-1} x, 3: y = A^{-1} x by the Gohberg-Semencul formula (TSFCDE_ALG_IDS_CONST
+ * only, after a march has passed level 1; j is ignored; TSFCDE_E_STATE before that).
+ * x, y: N host values.  Does not change the march state. */
 #define TSFCDE_OP_A 0
 #define TSFCDE_OP_B 1
 #define TSFCDE_OP_PINV 2
+#define TSFCDE_OP_AINV_GS 3
 int tsfcde_apply(tsfcde_ctx *ctx, int32_t op, int64_t j, const double *x, double *y);
 
 /* Operator product that allocates nothing (no counterpart in the paper; an addition of this

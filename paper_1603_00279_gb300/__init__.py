@@ -28,7 +28,8 @@ STATUS_NAMES = {
 PRECONDITIONERS = {"strang": 0, "tchan": 1, "none": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 INNER = {"auto": 0, "fp32": 1, "ff": 2}
-OPS = {"A": 0, "B": 1, "Pinv": 2}
+OPS = {"A": 0, "B": 1, "Pinv": 2, "Ainv_gs": 3}
+ALGORITHMS = {"ids": 0, "ids-const": 1}
 
 COEF_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 FIELD_FN = C.CFUNCTYPE(None, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -42,7 +43,8 @@ class Options(C.Structure):
                 ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
                 ("barrier_spin_log2", C.c_int32), ("test_skip_arrival", C.c_int32),
-                ("inner_precision", C.c_int32), ("autotune", C.c_int32)]
+                ("inner_precision", C.c_int32), ("autotune", C.c_int32),
+                ("algorithm", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -51,7 +53,7 @@ class Stats(C.Structure):
                 ("min_iterations", C.c_int32), ("max_residual", C.c_double),
                 ("status", C.c_int32), ("device_launches", C.c_int32),
                 ("device_ms", C.c_double), ("outer_iterations", C.c_int64),
-                ("escalated_levels", C.c_int32), ("pad_", C.c_int32)]
+                ("escalated_levels", C.c_int32), ("gsf_levels", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -158,7 +160,8 @@ class Solver:
                  stream: Optional[int] = None, precision: str = "fp64",
                  inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
                  outer_maxit: Optional[int] = None, barrier_spin_log2: Optional[int] = None,
-                 test_skip_arrival: bool = False, inner: str = "auto", autotune: bool = False):
+                 test_skip_arrival: bool = False, inner: str = "auto", autotune: bool = False,
+                 algorithm: str = "ids"):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
         self.h = (b - a) / (N + 1)
@@ -200,6 +203,7 @@ class Solver:
         opt.test_skip_arrival = 1 if test_skip_arrival else 0
         opt.inner_precision = INNER[inner]
         opt.autotune = 1 if autotune else 0
+        opt.algorithm = ALGORITHMS[algorithm]
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
@@ -318,7 +322,7 @@ class Batch:
 
     def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
-                 stream: Optional[int] = None, inner: str = "auto"):
+                 stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids"):
         self.lib = load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
@@ -339,6 +343,7 @@ class Batch:
         opt.device = device
         opt.stream = stream
         opt.inner_precision = INNER[inner]
+        opt.algorithm = ALGORITHMS[algorithm]
         h = C.c_void_p()
         _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
                "tsfcde_batch_setup")

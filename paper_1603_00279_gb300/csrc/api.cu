@@ -40,6 +40,7 @@ struct tsfcde_ctx {
   int budget = 4096;
   double tune_best_us = 0.0;
   int march_grid = 0;   // CTAs of the level-march launch (1: one-CTA team for small N)
+  bool gsf_ready = false;   // Gohberg-Semencul generators built (a march passed level 1)
 };
 
 namespace {
@@ -145,6 +146,7 @@ void tsfcde_default_options(tsfcde_options *opt) {
   opt->test_skip_arrival = 0;
   opt->inner_precision = TSFCDE_INNER_AUTO;
   opt->autotune = 0;
+  opt->algorithm = TSFCDE_ALG_IDS;
 }
 
 const char *tsfcde_strerror(int status) {
@@ -196,6 +198,8 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     if (!std::isfinite(gam[j]) || !std::isfinite(dp[j]) || !std::isfinite(dm[j])) return TSFCDE_E_NONFINITE;
     if (dp[j] < 0.0 || dm[j] < 0.0) return TSFCDE_E_INVALID_ARG;
     newsym[j] = (j <= 1) || gam[j] != gam[j - 1] || dp[j] != dp[j - 1] || dm[j] != dm[j - 1];
+    // Algorithm "... with constant coefficients" needs one level matrix for every j >= 1
+    if (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && j >= 2 && newsym[j]) return TSFCDE_E_INVALID_ARG;
   }
   const int R = c->opt.source_rank;
   std::vector<double> fdense;
@@ -242,6 +246,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   A.outer_maxit = c->opt.outer_maxit;
   A.spin_limit = 1ll << c->opt.barrier_spin_log2;
   A.test_skip = 0;
+  A.gsf = (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && M >= 2) ? 1 : 0;
   const bool mixed = A.precision == TSFCDE_MIXED;
 
   // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
@@ -364,6 +369,15 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     }
     A.lv_inner = cv.take<int>(M);
     A.lv_floor = cv.take<double>(M);
+    if (A.gsf) {
+      A.gx = cv.take<double>(Lp);
+      A.gy = cv.take<double>(Lp);
+      A.SL = cv.take<double2>(N + 1);
+      A.SR = cv.take<double2>(N + 1);
+      A.SL0 = cv.take<double2>(N + 1);
+      A.SR0 = cv.take<double2>(N + 1);
+      A.Y3 = cv.take<double2>(N);
+    }
     A.f_dense = f ? cv.take<double>((size_t)M * n) : nullptr;
     A.src_x = R > 0 ? cv.take<double>((size_t)R * n) : nullptr;
     A.src_t = R > 0 ? cv.take<double>((size_t)R * M) : nullptr;
@@ -503,6 +517,7 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
     return TSFCDE_E_INVALID_ARG;
   if (o.barrier_spin_log2 < 8 || o.barrier_spin_log2 > 40) return TSFCDE_E_INVALID_ARG;
   if (o.inner_precision < 0 || o.inner_precision > 2) return TSFCDE_E_INVALID_ARG;
+  if (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST) return TSFCDE_E_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
   tsfcde_ctx *c = new tsfcde_ctx();
@@ -577,6 +592,7 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     if (dst != TSFCDE_OK && dst != TSFCDE_E_NOT_CONVERGED) return dst;
     if (dst == TSFCDE_E_NOT_CONVERGED) worst = dst;
     c->level = e;
+    if (c->A.gsf && s <= 1 && 1 < e) c->gsf_ready = true;
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -590,7 +606,8 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
       std::vector<double> rs(nsteps);
       CK(cudaMemcpy(it.data(), c->A.iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(rs.data(), c->A.resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
-      if (c->A.precision == TSFCDE_MIXED) {
+      if (c->A.gsf) stats->gsf_levels = (int32_t)(j1 - std::max<int64_t>(j0, 1));
+      if (c->A.precision == TSFCDE_MIXED || c->A.gsf) {
         std::vector<int> oi(nsteps), es(nsteps);
         CK(cudaMemcpy(oi.data(), c->A.outer_iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(es.data(), c->A.escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
@@ -654,8 +671,9 @@ int tsfcde_get_history(tsfcde_ctx *c, int32_t *iters, double *resid, int64_t cou
 }
 
 int tsfcde_apply(tsfcde_ctx *c, int32_t op, int64_t j, const double *x, double *y) {
-  if (!c || !x || !y || op < 0 || op > 2 || j < 0 || j >= c->M) return TSFCDE_E_INVALID_ARG;
+  if (!c || !x || !y || op < 0 || op > 3 || j < 0 || j >= c->M) return TSFCDE_E_INVALID_ARG;
   if (op == TSFCDE_OP_PINV && c->A.precond == TSFCDE_PRECOND_NONE) return TSFCDE_E_INVALID_ARG;
+  if (op == TSFCDE_OP_AINV_GS && !(c->A.gsf && c->gsf_ready)) return TSFCDE_E_STATE;
   CK(cudaSetDevice(c->device));
   // vh and H are rewritten by every level before use, so they serve as scratch here
   CK(cudaMemcpyAsync(c->A.vh, x, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));

@@ -140,6 +140,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     A.inner_maxit = b->opt.inner_maxit;
     A.outer_maxit = b->opt.outer_maxit;
     A.spin_limit = 1ll << b->opt.barrier_spin_log2;
+    A.gsf = (b->opt.algorithm == TSFCDE_ALG_IDS_CONST && M >= 2) ? 1 : 0;
     b->n[i] = in[i].N;
     lgLmax = std::max(lgLmax, A.cp.lgL);
     nmax = std::max(nmax, in[i].N);
@@ -192,6 +193,14 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       A.status = cv.take<int>(4);
       A.lv_inner = cv.take<int>(M);
       A.lv_floor = cv.take<double>(M);
+      if (A.gsf) {   // Gohberg-Semencul generators and factor spectra persist across launches
+        A.gx = cv.take<double>(L);
+        A.gy = cv.take<double>(L);
+        A.SL = cv.take<double2>(N + 1);
+        A.SR = cv.take<double2>(N + 1);
+        A.SL0 = cv.take<double2>(N + 1);
+        A.SR0 = cv.take<double2>(N + 1);
+      }
       if (mixed) {
         A.twL32 = cv.take<float2>(L);
         A.twLff = cv.take<tsf::ffc>(L);
@@ -238,6 +247,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       C.SP = cs.take<double2>(Nmax + 1);
       C.Y1 = cs.take<double2>(Lmax);
       C.Y2 = cs.take<double2>(Lmax);
+      if (b->opt.algorithm == TSFCDE_ALG_IDS_CONST) C.Y3 = cs.take<double2>(Nmax);
       if (mixed) {
         C.g = cs.take<double>(Lmax);
         C.x32 = cs.take<float>(Lmax);
@@ -349,7 +359,8 @@ int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance 
   tsfcde_default_options(&o);
   if (opt) o = *opt;
   if (o.preconditioner < 0 || o.preconditioner > 2 ||
-      (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1)
+      (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1 ||
+      (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST))
     return TSFCDE_E_INVALID_ARG;
   for (int64_t i = 0; i < count; ++i) {
     const tsfcde_instance &I = inst[i];
@@ -460,7 +471,8 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
       std::vector<double> rs(nsteps);
       CK(cudaMemcpy(it.data(), b->inst[i].iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(rs.data(), b->inst[i].resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
-      if (b->opt.precision == TSFCDE_MIXED) {
+      const bool gsf = b->inst[i].gsf != 0;
+      if (b->opt.precision == TSFCDE_MIXED || gsf) {
         CK(cudaMemcpy(oi.data(), b->inst[i].outer_iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(es.data(), b->inst[i].escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
       }
@@ -469,10 +481,11 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
         stats->max_iterations = std::max(stats->max_iterations, it[k]);
         stats->min_iterations = std::min(stats->min_iterations, it[k]);
         stats->max_residual = std::max(stats->max_residual, rs[k]);
-        if (b->opt.precision == TSFCDE_MIXED) {
+        if (b->opt.precision == TSFCDE_MIXED || gsf) {
           stats->outer_iterations += oi[k];
           stats->escalated_levels += es[k];
         }
+        if (gsf && j0 + k >= 1) ++stats->gsf_levels;
       }
     }
   }

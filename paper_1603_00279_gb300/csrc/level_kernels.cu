@@ -75,14 +75,16 @@ __device__ __forceinline__ int team_threads() { return team().cnt * blockDim.x; 
 
 // ------------------------------------------------------------------------------------------------
 // Column pass of a four-step FFT: lines of P1 = 2^lg1 points, 2^lg2 of them, element m = m1*P2+m2.
-// INV: line m2 loads Yin[k1*P2 + m2] * conj(W^{m2 k1}) and is inverse-transformed.
+// INV: line m2 loads Yin[k1*P2 + m2] * conj(W^{m2 k1}) and is inverse-transformed (with Yin2
+//      given, the difference Yin - Yin2 is loaded).
 // body(m, z) -> next forward input (z: inverse result when INV, otherwise undefined).
 // FWD: forward transform of body's outputs, twiddle W^{m2 k1}, store Yout[k1*P2 + m2].
 // W^{e} = twG[e << tws] (tws = 1 for the half-length conv plan, 0 for the length-L plan).
 // ------------------------------------------------------------------------------------------------
 template <bool INV, bool FWD, typename T, class Body>
 __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *twG, int lg1, int lg2,
-                                         int tws, int cap, const T *Yin, T *Yout, Body body) {
+                                         int tws, int cap, const T *Yin, T *Yout, Body body,
+                                         const T *Yin2 = nullptr) {
   const int P1 = 1 << lg1, P2 = 1 << lg2;
   T *tw = static_cast<T *>(S.tw);
   int lo, hi;
@@ -94,7 +96,9 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *
     if (INV) {
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
-        a[(l << lg1) + k1] = cmulc(Yin[(k1 << lg2) + m2], twG[(m2 * k1) << tws]);
+        T v = Yin[(k1 << lg2) + m2];
+        if (Yin2) v = csub(v, Yin2[(k1 << lg2) + m2]);
+        a[(l << lg1) + k1] = cmulc(v, twG[(m2 * k1) << tws]);
       }
       __syncthreads();
       a = smem_fft<+1>(a, b, lg1, cnt, tw, lg1);
@@ -677,6 +681,187 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
 }
 
 // ------------------------------------------------------------------------------------------------
+// Constant coefficients: the Gohberg-Semencul formula (Section 3.2, after Eq. (3.4))
+//   A^{-1} = (L_p R_p - L0_p R0_p) / xi_0,  x = A^{-1} e_1 = (xi_k), y = A^{-1} e_n = (eta_k),
+//   L_p  lower triangular Toeplitz, first column x;   R_p  upper, first row (eta_{n-1}, ..., eta_0);
+//   L0_p strictly lower, first column (0, eta_0, ..., eta_{n-2});
+//   R0_p strictly upper, first row (0, xi_{n-1}, ..., xi_1).
+// Each factor is a Toeplitz product through the same L-point circulant embedding as A and B.
+// ------------------------------------------------------------------------------------------------
+
+// Spectra of the four factors from gx, gy (4 phases).  1/xi_0 is folded into L_p and L0_p.
+// Returns false when the kernel must stop; sets `st` to E_BREAKDOWN when xi_0 is 0 or not finite.
+__device__ bool gsf_spectra(const Args &A, const Smem &S, int &st) {
+  const int n = A.n, L = A.cp.L;
+  const double *gx = A.gx, *gy = A.gy;
+  const double sc = 1.0 / (4.0 * (double)A.cp.N);
+  // L_p: t_d = xi_d (0 <= d < n); R_p: t_0 = eta_{n-1}, t_{-d} = eta_{n-1-d} at index L - d
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
+#pragma unroll
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     v[h] = i < n ? gx[i] : 0.0;
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y2,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
+#pragma unroll
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     v[h] = i == 0 ? gy[n - 1] : (i > L - n ? gy[i + n - 1 - L] : 0.0);
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
+  if (!grid_sync(A)) return false;
+  const double xi0 = gx[0];
+  if (xi0 == 0.0 || !(xi0 == xi0) || isinf(xi0)) {
+    st = kEBreakdown;
+    return true;
+  }
+  row_pass<1, double2>(A, S, A.twL, A.Y1, nullptr, nullptr, A.SL, sc / xi0, -1);
+  row_pass<1, double2>(A, S, A.twL, A.Y2, nullptr, nullptr, A.SR, sc, -1);
+  if (!grid_sync(A)) return false;
+  // L0_p: t_d = eta_{d-1} (1 <= d < n); R0_p: t_{-d} = xi_{n-d} at index L - d (1 <= d < n)
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
+#pragma unroll
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     v[h] = (i >= 1 && i < n) ? gy[i - 1] : 0.0;
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
+  col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y2,
+                                 [&](int m, double2) -> double2 {
+                                   double v[2];
+#pragma unroll
+                                   for (int h = 0; h < 2; ++h) {
+                                     const int i = 2 * m + h;
+                                     v[h] = i > L - n ? gx[i + n - L] : 0.0;
+                                   }
+                                   return make_double2(v[0], v[1]);
+                                 });
+  if (!grid_sync(A)) return false;
+  row_pass<1, double2>(A, S, A.twL, A.Y1, nullptr, nullptr, A.SL0, sc / xi0, -1);
+  row_pass<1, double2>(A, S, A.twL, A.Y2, nullptr, nullptr, A.SR0, sc, -1);
+  return grid_sync(A);
+}
+
+// z = A^{-1} v by Algorithm "Compute z = A^{-1} v", from the forward column transform of v in Y1
+// (4 phases): z2 = R_p v and z1 = R0_p v share that transform; z4 = L_p z2 and z3 = L0_p z1;
+// z = z4 - z3 is formed in the last inverse column pass, whose body(m, z) sees z (zero beyond n)
+// and returns the next forward input (stored to Y1 when FWD).
+template <bool FWD, class Body>
+__device__ bool gsf_apply(const Args &A, const Smem &S, Body body) {
+  const int n = A.n;
+  auto trunc = [n](int m, double2 z) -> double2 {
+    if (2 * m >= n) z.x = 0.0;
+    if (2 * m + 1 >= n) z.y = 0.0;
+    return z;
+  };
+  row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, A.SR, nullptr, 0.0, -1);
+  row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y3, A.SR0, nullptr, 0.0, -1);
+  if (!grid_sync(A)) return false;
+  col_pass<true, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y2, trunc);
+  col_pass<true, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y3, A.Y3, trunc);
+  if (!grid_sync(A)) return false;
+  row_pass<0, double2>(A, S, A.twL, A.Y2, A.Y2, A.SL, nullptr, 0.0, -1);
+  row_pass<0, double2>(A, S, A.twL, A.Y3, A.Y3, A.SL0, nullptr, 0.0, -1);
+  if (!grid_sync(A)) return false;
+  col_pass<true, FWD, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                               [&](int m, double2 z) -> double2 { return body(m, trunc(m, z)); },
+                               A.Y3);
+  return grid_sync(A);
+}
+
+// Residual r = b - A v with the level spectrum S_A, from the forward column transform of v in Y1
+// (2 phases); b(m) gives the right-hand side pair; the forward column transform of r goes to Y1
+// and ||r||^2 is returned in tot[0].
+template <class RHS>
+__device__ bool residual_pass(const Args &A, const Smem &S, int &rb, RHS b, double (&tot)[3]) {
+  const int n = A.n;
+  row_pass<0, double2>(A, S, A.twL, A.Y1, A.Y2, A.SA, nullptr, 0.0, -1);
+  if (!grid_sync(A)) return false;
+  double acc[3] = {0.0, 0.0, 0.0};
+  col_pass<true, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, A.Y2, A.Y1,
+                                [&](int m, double2 z) -> double2 {
+                                  const double2 bv = b(m);
+                                  double2 rv = make_double2(bv.x - z.x, bv.y - z.y);
+                                  if (2 * m >= n) rv.x = 0.0;
+                                  if (2 * m + 1 >= n) rv.y = 0.0;
+                                  acc[0] += rv.x * rv.x + rv.y * rv.y;
+                                  return rv;
+                                });
+  write_partials(A, S, rb, acc);
+  if (!grid_sync(A)) return false;
+  read_partials(A, S, rb, tot);
+  rb ^= 1;
+  return true;
+}
+
+// Generators of the constant level matrix A (level symbols of j >= 1 in S_A, S_P): the systems
+// A x = e_1 and A y = e_n of Eq. (3.4) by the preconditioned CGS, the factor spectra, one
+// refinement of each generator with the inverse they define (x += A^{-1}(e_1 - A x)), and the
+// spectra again.  Returns the status; `its` counts the CGS iterations.
+__device__ int gsf_build(const Args &A, const Smem &S, const Krylov<double2> &V64, int &rb, int &its,
+                         bool &alive) {
+  const int n = A.n, L = A.cp.L;
+  its = 0;
+  alive = true;
+  for (int g = 0; g < 2; ++g) {
+    const int hot = g == 0 ? 0 : n - 1;
+    for (int i = team_tid(); i < L; i += team_threads()) {
+      const double e = i == hot ? 1.0 : 0.0;
+      A.x[i] = 0.0;
+      A.r[i] = e;
+      A.rt[i] = e;
+      A.uu[i] = e;
+      A.p[i] = e;
+    }
+    if (!(alive = grid_sync(A))) return kOK;
+    int it = 0;
+    double rel = 0.0;
+    const int st = cgs_solve<double2>(A, S, V64, 1.0, 1.0, A.tol, A.maxit, false, rb, it, rel, alive);
+    if (!alive) return kOK;
+    its += it;
+    if (st != kOK && st != kENotConverged) return st;
+    double *dst = g == 0 ? A.gx : A.gy;
+    for (int i = team_tid(); i < L; i += team_threads()) dst[i] = i < n ? A.x[i] : 0.0;
+    if (!(alive = grid_sync(A))) return kOK;
+  }
+  int st = kOK;
+  if (!(alive = gsf_spectra(A, S, st))) return kOK;
+  if (st != kOK) return st;
+  for (int g = 0; g < 2; ++g) {
+    double *gv = g == 0 ? A.gx : A.gy;
+    const int hot = g == 0 ? 0 : n - 1;
+    col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                   [&](int m, double2) -> double2 { return ld2(gv, m); });
+    if (!(alive = grid_sync(A))) return kOK;
+    double tot[3];
+    if (!(alive = residual_pass(A, S, rb,
+                                [&](int m) -> double2 {
+                                  return make_double2(2 * m == hot ? 1.0 : 0.0, 2 * m + 1 == hot ? 1.0 : 0.0);
+                                },
+                                tot)))
+      return kOK;
+    if (!(alive = gsf_apply<false>(A, S, [&](int m, double2 z) -> double2 {
+          const double2 v = ld2(gv, m);
+          st2(gv, m, make_double2(v.x + z.x, v.y + z.y));
+          return z;
+        })))
+      return kOK;
+  }
+  if (!(alive = gsf_spectra(A, S, st))) return kOK;
+  return st;
+}
+
+// ------------------------------------------------------------------------------------------------
 // the level kernel
 // ------------------------------------------------------------------------------------------------
 // Start of an inner solve on A d = r: d = 0, r = r~ = u = p = r rounded to the inner type;
@@ -734,8 +919,30 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
       if (!level_symbols(A, S, j)) return;
     }
     const bool useff = mixed && A.lv_inner[j] != 0;
+    // constant coefficients: levels j >= 1 share A, applied as A^{-1} by the Gohberg-Semencul formula
+    const bool gsf = A.gsf && j >= 1;
+    bool commit = j > j0;
+    int gen_its = 0;
+    if (gsf && j == 1) {
+      // the generator solves reuse the Krylov vectors: commit u^1 first
+      if (commit) {
+        ph_commit(A, 0);
+        if (!grid_sync(A)) return;
+        commit = false;
+      }
+      bool alive = true;
+      const int gst = gsf_build(A, S, V64, rb, gen_its, alive);
+      if (!alive) return;
+      if (gst != kOK) {
+        if (team().idx == 0 && threadIdx.x == 0) {
+          A.iters[j] = gen_its;
+          atomicCAS(A.status, 0, gst);
+          atomicExch(A.status + 1, 1);
+        }
+        return;   // consistent in every CTA
+      }
+    }
     // ---- RHS: g = B u^j - hscale * H^j + f^{j+sigma} (Eq. (3.1)) ----
-    const bool commit = j > j0;
     ph_history(A, j, commit);
     {
       const double *src = commit ? A.x : A.u;
@@ -764,6 +971,10 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
                                       }
                                     }
                                     const double2 g = make_double2(gv[0], gv[1]);
+                                    if (gsf) {   // g kept for the residual; its transform goes on to A^{-1}
+                                      st2(A.rt, m, g);
+                                      return g;
+                                    }
                                     st2(A.x, m, make_double2(0.0, 0.0));
                                     st2(A.r, m, g);
                                     if (mixed) {
@@ -787,6 +998,33 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
     bool alive = true;
     if (!(gnorm == gnorm) || isinf(gnorm)) {
       lstat = kENonFinite;
+    } else if (gsf) {
+      // u^{j+1} = A^{-1} g (Algorithm "Compute z = A^{-1} v"), the FP64 residual, and at most two
+      // refinements u += A^{-1}(g - A u) while it is above both tol and the FP64 floor
+      its = gen_its;
+      if (!gsf_apply<true>(A, S, [&](int m, double2 z) -> double2 {
+            st2(A.x, m, z);
+            return z;
+          }))
+        return;
+      outer = 1;
+      double prev = 0.0;
+      while (true) {
+        if (!residual_pass(A, S, rb, [&](int m) -> double2 { return ld2(A.rt, m); }, tot)) return;
+        rel = gnorm > 0.0 ? sqrt(tot[0]) / gnorm : 0.0;
+        if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
+        if (rel < A.tol || rel < A.lv_floor[j]) break;
+        if (outer >= 3 || (outer > 1 && rel > 0.5 * prev)) { lstat = kENotConverged; break; }
+        prev = rel;
+        if (!gsf_apply<true>(A, S, [&](int m, double2 z) -> double2 {
+              const double2 xv = ld2(A.x, m);
+              const double2 xn = make_double2(xv.x + z.x, xv.y + z.y);
+              st2(A.x, m, xn);
+              return xn;
+            }))
+          return;
+        ++outer;
+      }
     } else if (!mixed) {
       lstat = cgs_solve<double2>(A, S, V64, tot[0], gnorm, A.tol, A.maxit, true, rb, its, rel, alive);
       if (!alive) return;
@@ -860,7 +1098,10 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
     if (team().idx == 0 && threadIdx.x == 0) {
       A.iters[j] = its;
       A.resid[j] = rel;
-      if (mixed) {
+      if (gsf) {
+        A.outer_iters[j] = outer;
+        A.escalated[j] = 0;
+      } else if (mixed) {
         A.outer_iters[j] = outer;
         A.escalated[j] = esc;
       }
@@ -897,12 +1138,23 @@ __global__ void __launch_bounds__(kThreads, 1) history_kernel(Args A, int j) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}); x and y are padded device vectors.
+// diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}, 3: A^{-1} by the Gohberg-Semencul
+// formula); x and y are padded device vectors.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int j, const double *xin, double *yout) {
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
   const int n = A.n;
+  if (op == 3) {   // y = A^{-1} x by the Gohberg-Semencul formula (generators already built)
+    col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
+                                   [&](int m, double2) -> double2 { return ld2(xin, m); });
+    if (!grid_sync(A)) return;
+    gsf_apply<false>(A, S, [&](int m, double2 z) -> double2 {
+      st2(yout, m, z);
+      return z;
+    });
+    return;
+  }
   if (!level_symbols(A, S, j)) return;
   col_pass<false, true, double2>(A, S, A.twL, A.cp.lg1, A.cp.lg2, 1, A.cap_col, nullptr, A.Y1,
                                  [&](int m, double2) -> double2 { return ld2(xin, m); });
@@ -1023,7 +1275,7 @@ __global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T)
 __device__ __forceinline__ void patch_cta_scratch(Args &A, const CtaScratch &C) {
   A.x = C.x; A.r = C.r; A.rt = C.rt; A.p = C.p; A.q = C.q; A.uu = C.uu; A.vh = C.vh; A.H = C.H;
   A.xb = C.xb;
-  A.SA = C.SA; A.SB = C.SB; A.SP = C.SP; A.Y1 = C.Y1; A.Y2 = C.Y2; A.cprime = C.cprime;
+  A.SA = C.SA; A.SB = C.SB; A.SP = C.SP; A.Y1 = C.Y1; A.Y2 = C.Y2; A.Y3 = C.Y3; A.cprime = C.cprime;
   A.partials = C.partials; A.bar = C.bar;
   A.g = C.g; A.x32 = C.x32; A.r32 = C.r32; A.rt32 = C.rt32; A.p32 = C.p32; A.q32 = C.q32;
   A.uu32 = C.uu32; A.vh32 = C.vh32; A.SA32 = C.SA32; A.SP32 = C.SP32; A.Y1f = C.Y1f; A.Y2f = C.Y2f;

@@ -98,6 +98,11 @@ struct Args {
   ffc *SAff, *SPff;       // float-float spectra (rounded from FP64), N+1
   ffc *Y1ff, *Y2ff;       // float-float FFT work, L/2 each
   ffc *twLff;             // float-float twiddles, L
+  // constant coefficients: A^{(j+sigma)} = A for j >= 1, solved by the Gohberg-Semencul formula
+  int gsf;                // 1: levels j >= 1 compute u^{j+1} = A^{-1} g (no Krylov iterations)
+  double *gx, *gy;        // generators x = A^{-1} e_1, y = A^{-1} e_n (Eq. (3.4)); L each, zero tail
+  double2 *SL, *SR, *SL0, *SR0;   // spectra of L_p / xi_0, R_p, L0_p / xi_0, R0_p (permuted, N+1)
+  double2 *Y3;            // third FFT work buffer, N complex
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -434,7 +439,7 @@ inline void precision_control(double sigma, double beta, double eta, double q, d
 struct CtaScratch {
   double *x, *r, *rt, *p, *q, *uu, *vh, *H, *cprime, *partials, *g, *xb;
   unsigned *bar;
-  double2 *SA, *SB, *SP, *Y1, *Y2;
+  double2 *SA, *SB, *SP, *Y1, *Y2, *Y3;
   float *x32, *r32, *rt32, *p32, *q32, *uu32, *vh32;
   float2 *SA32, *SP32, *Y1f, *Y2f;
   ff *xff, *rff, *rtff, *pff, *qff, *uuff, *vhff;
