@@ -207,6 +207,69 @@ def run(prob, levels: Optional[int] = None, source: Optional[Callable] = None,
 
 
 # ----------------------------------------------------------------------------------------------
+# Rows of one level's equation without n x n matrices (checks at sizes where elimination is
+# impossible)
+# ----------------------------------------------------------------------------------------------
+
+
+def level_row(prob, j: int, i: int, omega: Optional[np.ndarray] = None):
+    """Row i of A^{(j+sigma)} and of B^{(j+sigma)} (Eq. (3.3)), entry by entry:
+        L[i,k] = q Q[i,k] + kappa_+ omega_{i-k+1} + kappa_- omega_{k-i+1}
+                 (Q[i,i+1] = 1, Q[i,i-1] = -1; omega_m = 0 for m < 0, Eq. (3.2)),
+        A[i,:] = eta e_i - sigma L[i,:],  B[i,:] = eta e_i + (1 - sigma) L[i,:]."""
+    n = prob.n
+    sigma = 1.0 - prob.alpha / 2.0
+    w = wsgd_weights(prob.beta, n + 1) if omega is None else omega
+    e, q, kp, km = level_scalars(prob, j)
+    k = np.arange(n)
+    dW = i - k + 1                       # W[i,k] = omega_{i-k+1}
+    dWt = k - i + 1                      # W^T[i,k] = W[k,i] = omega_{k-i+1}
+    Lrow = kp * np.where(dW >= 0, w[np.clip(dW, 0, n + 1)], 0.0)
+    Lrow = Lrow + km * np.where(dWt >= 0, w[np.clip(dWt, 0, n + 1)], 0.0)
+    if i + 1 < n:
+        Lrow[i + 1] += q
+    if i - 1 >= 0:
+        Lrow[i - 1] -= q
+    Arow = -sigma * Lrow
+    Brow = (1.0 - sigma) * Lrow
+    Arow[i] += e
+    Brow[i] += e
+    return Arow, Brow
+
+
+def level_equation_rows(prob, j: int, rows, levels: List[np.ndarray], u_next: np.ndarray,
+                        source: Optional[Callable] = None):
+    """Rows of the level-j equation of Eq. (3.1) evaluated at given level vectors u^0..u^j
+    (`levels`) and u^{j+1} (`u_next`), O(n) work per row:
+        g_i  = (B u^j)_i - tau^{-alpha}/Gamma(2-alpha) sum_{s<j} c^{(j)}_{j-s} (u^{s+1}_i - u^s_i)
+               + f(x_i, t_{j+sigma}),
+        Au_i = (A u^{j+1})_i.
+    Returns (g, Au) over `rows`."""
+    n = prob.n
+    w = wsgd_weights(prob.beta, n + 1)
+    sigma = 1.0 - prob.alpha / 2.0
+    hist_scale = prob.tau ** (-prob.alpha) / math.gamma(2.0 - prob.alpha)
+    c = c_coeffs(prob.alpha, j) if j >= 1 else None
+    f = source if source is not None else prob.f
+    x = prob.grid()
+    g = np.empty(len(rows))
+    Au = np.empty(len(rows))
+    for r, i in enumerate(rows):
+        Arow, Brow = level_row(prob, j, int(i), w)
+        gi = float(Brow @ levels[j])
+        if j >= 1:
+            H = 0.0
+            for s_ in range(j):
+                H += c[j - s_] * (levels[s_ + 1][i] - levels[s_][i])
+            gi -= hist_scale * H
+        if f is not None:
+            gi += float(np.asarray(f(x[i:i + 1], (j + sigma) * prob.tau))[0])
+        g[r] = gi
+        Au[r] = float(Arow @ u_next)
+    return g, Au
+
+
+# ----------------------------------------------------------------------------------------------
 # Constant coefficients (Section 3.2): the Gohberg-Semencul formula after Eq. (3.4), Algorithm
 # "Compute z = A^{-1} v" and Algorithm "Practical implementation of IDS with constant
 # coefficients".  Dense matrices throughout; no FFT.

@@ -217,3 +217,30 @@ def test_gaussian_elimination_vs_mpmath():
     for j in range(p.M + 1):
         ref = np.array([float(v) for v in u[j]])
         np.testing.assert_allclose(lv[j], ref, rtol=1e-12, atol=1e-15)
+
+
+def test_level_rows_equal_dense_matrices():
+    """The row-wise evaluation of Eq. (3.1) used at sizes where elimination is impossible gives
+    the rows of the dense A, B and right-hand side, boundary rows included."""
+    prob = W.config_small(n=40, M=6)
+    lv = O.run(prob)
+    n = prob.n
+    rows = [0, 1, 2, 17, n - 3, n - 2, n - 1]
+    for j in [0, 1, 4]:
+        A, B = O.level_matrices(prob, j)
+        Arow0, Brow0 = O.level_row(prob, j, 0)
+        for i in rows:
+            a, b = O.level_row(prob, j, i)
+            assert np.array_equal(a, A[i]) and np.array_equal(b, B[i])
+        g, Au = O.level_equation_rows(prob, j, rows, lv[:j + 1], lv[j + 1])
+        # the elimination march solved A u^{j+1} = g: both sides agree to rounding
+        scale = np.abs(A[rows]) @ np.abs(lv[j + 1])
+        assert np.all(np.abs(g - Au) <= 1e-13 * scale)
+        # and g is the right-hand side the march used: recompute it densely
+        gd = B @ lv[j]
+        if j >= 1:
+            c = O.c_coeffs(prob.alpha, j)
+            H = sum(c[j - s] * (lv[s + 1] - lv[s]) for s in range(j))
+            gd = gd - prob.tau ** (-prob.alpha) / math.gamma(2 - prob.alpha) * H
+        gd = gd + prob.f(prob.grid(), (j + 1 - prob.alpha / 2) * prob.tau)
+        assert np.allclose(g, gd[rows], rtol=1e-14, atol=1e-14 * np.abs(gd).max())
