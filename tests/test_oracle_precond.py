@@ -107,3 +107,20 @@ def test_pcgs_without_preconditioner_is_slow():
     g = B @ p.phi(p.grid())
     _, its, _ = O.pcgs(A, g, None, maxit=60)
     assert its == 60
+
+
+@pytest.mark.parametrize("j", [0, 1])
+def test_preconditioned_spectrum_clusters_at_one(j):
+    """Figs. 1-2 (Section 4): Example 1 at N = M = 128, alpha = 0.9, beta = 1.8, levels j = 0, 1.
+    The eigenvalues of P^{-1} A (Strang) cluster at 1 except for about 6-10 outliers and stay
+    away from 0, while those of A spread over two orders of magnitude.  Outlier reading:
+    |lambda - 1| > 1e-3 (the paper gives no threshold)."""
+    prob = W.example1(127, 128, 0.9, 1.8)
+    A, _ = O.level_matrices(prob, j)
+    P = O.preconditioner_matrix(prob, j, "strang")
+    lam = np.linalg.eigvals(np.linalg.solve(P, A))
+    lamA = np.abs(np.linalg.eigvals(A))
+    outliers = int((np.abs(lam - 1.0) > 1e-3).sum())
+    assert 6 <= outliers <= 10, outliers
+    assert np.abs(lam).min() > 0.5
+    assert lamA.max() / lamA.min() > 100.0
