@@ -607,7 +607,7 @@ def main():
     ap.add_argument("--workload", default="large")
     ap.add_argument("--precond", default=None, choices=[None, "strang", "tchan", "none"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"],
-                    help="default: fp64, or mixed for the mixed workload")
+                    help="default: fp64, or mixed for the mixed and history workloads")
     ap.add_argument("--levels", type=int, default=None, help="override M (exploration only)")
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -624,7 +624,7 @@ def main():
     _ARGS = args
     p = workload(args.workload, args.precond)
     if args.precision is None:
-        args.precision = "mixed" if args.workload == "mixed" else "fp64"
+        args.precision = "mixed" if args.workload in ("mixed", "history") else "fp64"
     if args.levels and args.workload not in ("batch", "history"):
         p.M = args.levels
     if args.levels and args.workload == "history":

@@ -53,13 +53,21 @@ __device__ __forceinline__ int lp_max_of(const Args &A) {
 }
 
 // Fill S.tw with the line twiddles e^{-2 pi i m / 2^lgP}, m < 2^lgP (a subset of the L table).
+// Skipped when the table already holds them (the tag is CTA-uniform: read after a barrier).
 template <typename T>
 __device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S, const T *twG, int lgP) {
   __syncthreads();
+  TwTag &tg = tw_tag();
+  if (tg.tab == static_cast<const void *>(twG) && tg.dst == S.tw && tg.lg == lgP) return;
   const int P = 1 << lgP, sh = A.cp.lgL - lgP;
   T *tw = static_cast<T *>(S.tw);
   for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = twG[m << sh];
   __syncthreads();
+  if (threadIdx.x == 0) {
+    tg.tab = twG;
+    tg.dst = S.tw;
+    tg.lg = lgP;
+  }
 }
 
 // Contiguous item range of this CTA: [lo, hi).

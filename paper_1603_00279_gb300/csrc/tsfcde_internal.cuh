@@ -319,6 +319,18 @@ __device__ __forceinline__ TeamInfo &team() {
   return t;
 }
 
+// What the shared-memory line-twiddle table holds (source table, destination, line length), so
+// that a pass whose line twiddles are already there does not reload them.  Reset at kernel start.
+struct TwTag {
+  const void *tab;
+  const void *dst;
+  int lg;
+};
+__device__ __forceinline__ TwTag &tw_tag() {
+  __shared__ TwTag t;
+  return t;
+}
+
 // Per-CTA count of grid barriers passed in this launch.
 __device__ __forceinline__ unsigned long long &bar_count() {
   __shared__ unsigned long long k;
@@ -331,6 +343,7 @@ __device__ __forceinline__ void grid_sync_init() {
     team().idx = blockIdx.x;
     team().cnt = gridDim.x;
     team().grid = 1;
+    tw_tag().tab = nullptr;
   }
   __syncthreads();
 }
@@ -341,6 +354,7 @@ __device__ __forceinline__ void cta_team_init() {
     team().idx = 0;
     team().cnt = 1;
     team().grid = 0;
+    tw_tag().tab = nullptr;
   }
   __syncthreads();
 }
