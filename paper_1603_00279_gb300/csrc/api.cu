@@ -41,6 +41,7 @@ struct tsfcde_ctx {
   double tune_best_us = 0.0;
   int march_grid = 0;   // CTAs of the level-march launch (1: one-CTA team for small N)
   bool gsf_ready = false;   // Gohberg-Semencul generators built (a march passed level 1)
+  size_t smem_cta = 0;      // dynamic shared memory of the one-CTA march for the final plan
 };
 
 namespace {
@@ -271,15 +272,9 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     }
   }
 
-  // ---- small instances: the march runs in one CTA (level_kernel_cta) ----
+  // ---- small instances: the march runs in one CTA (level_kernel_cta; shared memory is sized
+  //      for the final plan at the end of setup) ----
   c->march_grid = (A.cp.N <= kCtaMarchMaxN) ? 1 : c->grid;
-  if (c->march_grid == 1) {
-    Args B = A;
-    set_caps(B, 1, c->budget);
-    const size_t sm1 = tsf::level_smem_bytes(B);
-    CK(cudaFuncSetAttribute(tsf::level_kernel_cta_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)std::max(sm1, c->smem)));
-  }
 
   // ---- device memory: one arena + the history ring ----
   const size_t Lp = (size_t)L;
@@ -492,6 +487,14 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     st = run_setup();
     if (st) return st;
   }
+  if (c->march_grid == 1) {
+    Args B = A;
+    set_caps(B, 1, c->budget);
+    c->smem_cta = tsf::level_smem_bytes(B);
+    if (c->smem_cta > smem_limit) return TSFCDE_E_INVALID_ARG;
+    CK(cudaFuncSetAttribute(tsf::level_kernel_cta_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->smem_cta));
+  }
   c->level = 0;
   return TSFCDE_OK;
 }
@@ -574,7 +577,7 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     if (c->march_grid == 1) {
       Args B = c->A;   // one-CTA team: every pass item belongs to the single CTA
       set_caps(B, 1, c->budget);
-      st = tsf::launch_levels(B, 1, tsf::level_smem_bytes(B), c->stream, (int)s, (int)e);
+      st = tsf::launch_levels(B, 1, c->smem_cta, c->stream, (int)s, (int)e);
     } else {
       st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
     }
