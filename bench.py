@@ -62,6 +62,43 @@ def roofline(kernel, flops, kernel_ms, precision, outer_steps=0):
             "frac": achieved / peak, "traffic": None, "peak_source": src}
 
 
+class Ranks:
+    """One process per GPU (torchrun env): world, rank, local device, the process group."""
+
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+
+    def init(self):
+        import torch
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.dist = dist
+        torch.cuda.set_device(self.local)
+        return self
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        from paper_1603_00279_gb300.multirank import max_over_ranks
+        return max_over_ranks(x, self.dist, device="cuda")
+
+
+def shard_instances(probs, ranks):
+    """This rank's instances: cost-balanced shards of the whole set (strong scaling)."""
+    from paper_1603_00279_gb300.multirank import instance_cost, shard
+    if len(probs) < ranks.world:
+        raise SystemExit(f"{len(probs)} instances cannot be shared by {ranks.world} ranks "
+                         "(use --instances >= the number of GPUs)")
+    costs = [instance_cost(q.n, q.M) for q in probs]
+    return [probs[i] for i in shard(costs, ranks.world, ranks.rank)]
+
+
 def workload(name: str, precond):
     if name == "large":
         p = W.config_large()
@@ -409,13 +446,19 @@ def run_native(args, p):
         dist.destroy_process_group()
 
 
-def run_native_batch(args, probs):
-    """Batched workload: every instance marched through all M levels per step."""
+def run_native_batch(args, probs_all):
+    """Batched workload: every instance marched through all M levels per step.  With several
+    ranks each marches a cost-balanced shard of the instances (no collective on the data path);
+    the step time is the slowest rank's."""
     import torch
-    torch.cuda.set_device(0)
+    ranks = Ranks().init()
     from paper_1603_00279_gb300 import build
-    build.build()
+    if ranks.rank == 0 or ranks.world == 1:
+        build.build()
+    ranks.barrier()
     import paper_1603_00279_gb300 as P
+    probs = shard_instances(probs_all, ranks)
+    ntot_all = sum(p.n for p in probs_all)
     M = probs[0].M
     precond = args.precond or "strang"
     stream = torch.cuda.Stream()
@@ -431,17 +474,19 @@ def run_native_batch(args, probs):
     for _ in range(args.warmup):
         one_step()
     stats = []
+    ranks.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(ranks.local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             stats.append(one_step())
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    value = ntot * M * args.steps / (ms / 1e3)
+    ranks.barrier()
+    ms = ranks.max(e0.elapsed_time(e1))
+    value = ntot_all * M * args.steps / (ms / 1e3)
     kernel_ms = float(np.mean([st["device_ms"] for st in stats]))
     flops = 0.0
     its_all = []
@@ -465,24 +510,29 @@ def run_native_batch(args, probs):
         b.set_initial(u0.data_ptr())
         b.step(M)
         b.get_all(uM.data_ptr())
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = ranks.max((time.perf_counter() - t0) / e2e_steps)
     b.close()
-    ns = np.array([p.n for p in probs])
+    if ranks.rank != 0:
+        return
+    ns = np.array([p.n for p in probs_all])
     line = {
-        "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": 1,
+        "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": ranks.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if ranks.world > 1 else "weak",
+        "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 inner / f64 refinement",
         "data": "synthetic (seeded instances, sine-mode initial values, f = 0)",
-        "config": {"workload": "tsfcde_batch", "instances": len(probs), "M": M,
-                   "n_min": int(ns.min()), "n_max": int(ns.max()), "sum_n": int(ntot),
-                   "preconditioner": precond, "tol": 1e-12, "parallelism": "replicas1",
+        "config": {"workload": "tsfcde_batch", "instances": len(probs_all), "M": M,
+                   "n_min": int(ns.min()), "n_max": int(ns.max()), "sum_n": int(ntot_all),
+                   "preconditioner": precond, "tol": 1e-12,
+                   "parallelism": (f"instance shards over {ranks.world} ranks (cost-balanced)"
+                                   if ranks.world > 1 else "replicas1"),
                    "algorithm": ("IDS with constant coefficients (Gohberg-Semencul, levels >= 1)"
                                  if const else "IDS (PCGS every level)"),
-                   "updates_per_step": int(ntot * M),
-                   "l2": "inputs larger than L2 (history %.1f GB)" % (ntot * M * 8 / 1e9)},
-        "e2e": {"value": ntot * M / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": 8 * int(ntot),
-                "d2h_bytes_per_step": 8 * int(ntot)},
+                   "updates_per_step": int(ntot_all * M),
+                   "l2": "inputs larger than L2 (history %.1f GB)" % (ntot_all * M * 8 / 1e9)},
+        "e2e": {"value": ntot_all * M / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": 8 * int(ntot_all), "d2h_bytes_per_step": 8 * int(ntot_all)},
         "gpu_launches": int(sum(st["device_launches"] for st in stats)),
         "roofline": roofline("batch_level_kernel", flops, kernel_ms, args.precision),
         "cgs_iterations": {"mean": float(its_all.mean()), "min": int(its_all.min()),
@@ -522,12 +572,16 @@ def run_native_history(args, probs):
     (each holds a 17 GB FP64 history), FP64 history accumulation, the given precision for the
     solves."""
     import torch
-    torch.cuda.set_device(0)
+    ranks = Ranks().init()
     from paper_1603_00279_gb300 import build
-    build.build()
+    if ranks.rank == 0 or ranks.world == 1:
+        build.build()
+    ranks.barrier()
     import paper_1603_00279_gb300 as P
     stream = torch.cuda.Stream()
-    ntot = sum(q.n * q.M for q in probs)
+    probs_all = probs
+    probs = shard_instances(probs_all, ranks)
+    ntot = sum(q.n * q.M for q in probs_all)
     ctxs = [P.Solver.from_problem(q, source="separable", stream=stream.cuda_stream,
                                   precision=args.precision, maxit=args.maxit) for q in probs]
 
@@ -540,15 +594,17 @@ def run_native_history(args, probs):
 
     for _ in range(args.warmup):
         one_step()
+    ranks.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(ranks.local) as clk:
         e0.record(stream)
         stats = [one_step() for _ in range(args.steps)]
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ranks.barrier()
+    ms = ranks.max(e0.elapsed_time(e1))
     # history phase at the last level of the first instance
     q0, s0 = probs[0], ctxs[0]
     jh = q0.M - 1
@@ -578,15 +634,18 @@ def run_native_history(args, probs):
         co = {"E_M/2": eh, "E_M": errs[0], "CO_tau": math.log2(eh / errs[0])}
     for s in ctxs:
         s.close()
+    if ranks.rank != 0:
+        return
     its = [st["total_iterations"] / max(1, st["levels_advanced"]) for step in stats for st in step]
     line = {"metric": "grid-point updates/s", "value": ntot * args.steps / (ms / 1e3),
-            "unit": "updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "unit": "updates/s", "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if ranks.world > 1 else "weak",
             "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32/ff inner / f64 refinement, f64 history",
             "data": "synthetic (manufactured solution)",
-            "config": {"workload": "tsfcde_history", "instances": len(probs), "n": probs[0].n,
-                       "M": probs[0].M, "alpha_beta": [[q.alpha, q.beta] for q in probs],
+            "config": {"workload": "tsfcde_history", "instances": len(probs_all), "n": probs[0].n,
+                       "M": probs[0].M, "alpha_beta": [[q.alpha, q.beta] for q in probs_all],
                        "history_bytes_per_instance": 8 * probs[0].n * probs[0].M},
             "history_roofline": {"kernel": "history phase (level M-1)", "bound": "hbm",
                                  "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak[0],

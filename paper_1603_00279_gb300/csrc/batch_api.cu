@@ -31,6 +31,10 @@ struct tsfcde_batch {
   unsigned *d_next = nullptr;
   double *d_u0 = nullptr;            // all instances' u^0, concatenated (N_i doubles each)
   double *d_uout = nullptr;          // staging for tsfcde_batch_get_all (same layout)
+  // per-instance status words and per-level histories, contiguous over instances so that one
+  // copy reads them all: status K x 4, iters / resid / outer / escalated K x M
+  int *d_status = nullptr, *d_iters = nullptr, *d_outer = nullptr, *d_esc = nullptr;
+  double *d_resid = nullptr;
   size_t u_total = 0;
   int grid = 0;
   size_t smem = 0;
@@ -164,6 +168,11 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
   for (int pass = 0; pass < 2; ++pass) {
     cv.off = 0;
     cv.base = pass ? b->arena : nullptr;
+    b->d_status = cv.take<int>((size_t)K * 4);
+    b->d_iters = cv.take<int>((size_t)K * M);
+    b->d_resid = cv.take<double>((size_t)K * M);
+    b->d_outer = cv.take<int>((size_t)K * M);
+    b->d_esc = cv.take<int>((size_t)K * M);
     for (int64_t i = 0; i < K; ++i) {
       Args &A = b->inst[i];
       const size_t L = A.cp.L, N = A.cp.N, n = A.n;
@@ -186,11 +195,11 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
       A.lv_newsym = cv.take<int>(M);
       A.hc = cv.take<double>(M + 2);
       A.hl = cv.take<double>(M + 2);
-      A.iters = cv.take<int>(M);
-      A.resid = cv.take<double>(M);
-      A.outer_iters = cv.take<int>(M);
-      A.escalated = cv.take<int>(M);
-      A.status = cv.take<int>(4);
+      A.iters = b->d_iters + (size_t)i * M;
+      A.resid = b->d_resid + (size_t)i * M;
+      A.outer_iters = b->d_outer + (size_t)i * M;
+      A.escalated = b->d_esc + (size_t)i * M;
+      A.status = b->d_status + (size_t)i * 4;
       A.lv_inner = cv.take<int>(M);
       A.lv_floor = cv.take<double>(M);
       if (A.gsf) {   // Gohberg-Semencul generators and factor spectra persist across launches
@@ -342,10 +351,11 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
   int st = tsf::launch_batch(B, b->grid, b->smem, b->stream, 1, 0, 0);
   if (st) return st;
   CK(cudaStreamSynchronize(b->stream));
-  for (int64_t i = 0; i < K; ++i) {
-    int h[2];
-    CK(cudaMemcpy(h, b->inst[i].status, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0]) return h[0];
+  {
+    std::vector<int> h((size_t)K * 4);
+    CK(cudaMemcpy(h.data(), b->d_status, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < K; ++i)
+      if (h[(size_t)i * 4]) return h[(size_t)i * 4];
   }
   return tsfcde_batch_reset(b);
 }
@@ -439,7 +449,7 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
   float ms = 0.f;
   int launches = 0;
   if (nsteps > 0) {
-    for (int64_t i = 0; i < b->count; ++i) CK(cudaMemsetAsync(b->inst[i].status, 0, 4 * sizeof(int), b->stream));
+    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->count * 4 * sizeof(int), b->stream));
     CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
     tsf::BatchArgs B;
     B.count = (int)b->count;
@@ -461,31 +471,46 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->min_iterations = 1 << 30;
   }
-  for (int64_t i = 0; i < b->count && nsteps > 0; ++i) {
-    int h[2];
-    CK(cudaMemcpy(h, b->inst[i].status, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0] && h[0] != TSFCDE_E_NOT_CONVERGED) return h[0];
-    if (h[0]) worst = h[0];
+  if (nsteps > 0) {
+    const int64_t K = b->count, M = b->M;
+    std::vector<int> h((size_t)K * 4);
+    CK(cudaMemcpy(h.data(), b->d_status, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < K; ++i) {
+      const int hi = h[(size_t)i * 4];
+      if (hi && hi != TSFCDE_E_NOT_CONVERGED) return hi;
+      if (hi) worst = hi;
+    }
     if (stats) {
-      std::vector<int> it(nsteps), oi(nsteps), es(nsteps);
-      std::vector<double> rs(nsteps);
-      CK(cudaMemcpy(it.data(), b->inst[i].iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(rs.data(), b->inst[i].resid + j0, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
-      const bool gsf = b->inst[i].gsf != 0;
-      if (b->opt.precision == TSFCDE_MIXED || gsf) {
-        CK(cudaMemcpy(oi.data(), b->inst[i].outer_iters + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(es.data(), b->inst[i].escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+      // the [j0, j1) window of every instance's per-level history, one strided copy each
+      const bool mixed = b->opt.precision == TSFCDE_MIXED;
+      const bool gsf = b->opt.algorithm == TSFCDE_ALG_IDS_CONST && M >= 2;
+      std::vector<int> it((size_t)K * nsteps), oi, es;
+      std::vector<double> rs((size_t)K * nsteps);
+      CK(cudaMemcpy2D(it.data(), nsteps * sizeof(int), b->d_iters + j0, M * sizeof(int),
+                      nsteps * sizeof(int), K, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy2D(rs.data(), nsteps * sizeof(double), b->d_resid + j0, M * sizeof(double),
+                      nsteps * sizeof(double), K, cudaMemcpyDeviceToHost));
+      if (mixed || gsf) {
+        oi.resize((size_t)K * nsteps);
+        es.resize((size_t)K * nsteps);
+        CK(cudaMemcpy2D(oi.data(), nsteps * sizeof(int), b->d_outer + j0, M * sizeof(int),
+                        nsteps * sizeof(int), K, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy2D(es.data(), nsteps * sizeof(int), b->d_esc + j0, M * sizeof(int),
+                        nsteps * sizeof(int), K, cudaMemcpyDeviceToHost));
       }
-      for (int64_t k = 0; k < nsteps; ++k) {
-        stats->total_iterations += it[k];
-        stats->max_iterations = std::max(stats->max_iterations, it[k]);
-        stats->min_iterations = std::min(stats->min_iterations, it[k]);
-        stats->max_residual = std::max(stats->max_residual, rs[k]);
-        if (b->opt.precision == TSFCDE_MIXED || gsf) {
-          stats->outer_iterations += oi[k];
-          stats->escalated_levels += es[k];
+      for (int64_t i = 0; i < K; ++i) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+          const size_t x = (size_t)i * nsteps + k;
+          stats->total_iterations += it[x];
+          stats->max_iterations = std::max(stats->max_iterations, it[x]);
+          stats->min_iterations = std::min(stats->min_iterations, it[x]);
+          stats->max_residual = std::max(stats->max_residual, rs[x]);
+          if (mixed || gsf) {
+            stats->outer_iterations += oi[x];
+            stats->escalated_levels += es[x];
+          }
+          if (gsf && j0 + k >= 1) ++stats->gsf_levels;
         }
-        if (gsf && j0 + k >= 1) ++stats->gsf_levels;
       }
     }
   }
