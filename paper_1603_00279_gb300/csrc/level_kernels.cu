@@ -444,6 +444,11 @@ __device__ bool level_symbols(const Args &A, const Smem &S, int j) {
 }
 
 // Commit of level j-1 (when commit), history sum of Lemma 1 for level j into H, contiguous.
+#ifndef TSFCDE_HIST_UNROLL
+#define TSFCDE_HIST_UNROLL 16
+#endif
+constexpr int kHistUnroll = TSFCDE_HIST_UNROLL;
+
 __device__ void ph_history(const Args &A, int j, bool commit) {
   const int npair = (A.n + 1) >> 1;
   const long long st = A.ring_stride;
@@ -462,17 +467,17 @@ __device__ void ph_history(const Args &A, int j, bool commit) {
       // s = 0 term: c^{(j)}_j = a_j - b_j; 1 <= s <= j-1: c^{(j)}_{j-s} = a + b - b (Lemma 1)
       const int smax = commit ? j - 1 : j;   // levels read from the ring
       int s = 0;
-      for (; s + 4 <= smax; s += 4) {
-        const double2 d0 = ring2[(s + 0) * (st >> 1) + t];
-        const double2 d1 = ring2[(s + 1) * (st >> 1) + t];
-        const double2 d2 = ring2[(s + 2) * (st >> 1) + t];
-        const double2 d3 = ring2[(s + 3) * (st >> 1) + t];
-        const double c0 = s == 0 ? A.hl[j] : A.hc[j - s];
-        const double c1 = A.hc[j - s - 1], c2 = A.hc[j - s - 2], c3 = A.hc[j - s - 3];
-        hx += c0 * d0.x; hy += c0 * d0.y;
-        hx += c1 * d1.x; hy += c1 * d1.y;
-        hx += c2 * d2.x; hy += c2 * d2.y;
-        hx += c3 * d3.x; hy += c3 * d3.y;
+      // kHistUnroll ring rows in flight per thread (16-byte loads), summed in order of s
+      for (; s + kHistUnroll <= smax; s += kHistUnroll) {
+        double2 d[kHistUnroll];
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) d[u] = ring2[(s + u) * (st >> 1) + t];
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+          const double c = (s + u) == 0 ? A.hl[j] : A.hc[j - s - u];
+          hx += c * d[u].x;
+          hy += c * d[u].y;
+        }
       }
       for (; s < smax; ++s) {
         const double2 d = ring2[s * (st >> 1) + t];
