@@ -322,7 +322,8 @@ class Batch:
 
     def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
-                 stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids"):
+                 stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids",
+                 inner_tol: Optional[float] = None):
         self.lib = load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
@@ -344,6 +345,8 @@ class Batch:
         opt.stream = stream
         opt.inner_precision = INNER[inner]
         opt.algorithm = ALGORITHMS[algorithm]
+        if inner_tol is not None:
+            opt.inner_tol = inner_tol
         h = C.c_void_p()
         _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
                "tsfcde_batch_setup")

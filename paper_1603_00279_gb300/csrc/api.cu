@@ -140,7 +140,7 @@ void tsfcde_default_options(tsfcde_options *opt) {
   opt->source_rank = 0;
   opt->levels_per_launch = 0;
   opt->stream = nullptr;
-  opt->inner_tol = 1e-5;
+  opt->inner_tol = 1e-3;
   opt->inner_maxit = 1000;
   opt->outer_maxit = 12;
   opt->barrier_spin_log2 = 23;
