@@ -118,7 +118,8 @@ def workload(name: str, precond):
 
 
 def describe(p) -> dict:
-    return {"workload": f"tsfcde_{p.name}", "n": p.n, "M": p.M, "alpha": p.alpha, "beta": p.beta,
+    name = "history" if p.name.startswith("history") else p.name
+    return {"workload": f"tsfcde_{name}", "n": p.n, "M": p.M, "alpha": p.alpha, "beta": p.beta,
             "preconditioner": p.preconditioner, "tol": p.tol, "source": "separable(4)",
             "updates_per_step": p.n * p.M}
 
@@ -221,8 +222,11 @@ def oracle_sample(p, budget_s: float = 15.0):
     many levels as fit the budget; returns (updates/s, description, cores)."""
     import oracle as O
     n_s = min(p.n, 2047)
-    cls = {"large": W.config_large, "small": W.config_small, "mixed": W.config_mixed}[p.name]
-    q = cls(n=n_s, M=p.M)
+    if p.name.startswith("history"):
+        q = W.config_history(n=n_s, M=p.M)[int(p.name[len("history"):])]
+    else:
+        cls = {"large": W.config_large, "small": W.config_small, "mixed": W.config_mixed}[p.name]
+        q = cls(n=n_s, M=p.M)
     q.preconditioner = p.preconditioner
     t0 = time.perf_counter()
     levels = 1
@@ -690,7 +694,10 @@ def main():
         for q in p:
             q.M = args.levels
     if args.workload == "history":
-        run_native_history(args, p)
+        if args.impl == "reference":
+            run_reference(args, p[0])
+        else:
+            run_native_history(args, p)
         return
     if args.workload == "batch":
         if args.levels:
