@@ -914,18 +914,24 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   const int n = A.n;
   const bool mixed = A.precision == kMixed;
   int rb = 0;
-  Krylov<double2> V64;
-  V64.x = A.x; V64.r = A.r; V64.rt = A.rt; V64.p = A.p; V64.q = A.q; V64.uu = A.uu; V64.vh = A.vh;
-  V64.xb = A.xb;
-  V64.SA = A.SA; V64.SP = A.SP; V64.Y1 = A.Y1; V64.Y2 = A.Y2; V64.twG = A.twL;
-  Krylov<float2> V32;
-  V32.x = A.x32; V32.r = A.r32; V32.rt = A.rt32; V32.p = A.p32; V32.q = A.q32; V32.uu = A.uu32;
-  V32.xb = A.x32b;
-  V32.vh = A.vh32; V32.SA = A.SA32; V32.SP = A.SP32; V32.Y1 = A.Y1f; V32.Y2 = A.Y2f; V32.twG = A.twL32;
-  Krylov<ffc> VF;
-  VF.x = A.xff; VF.r = A.rff; VF.rt = A.rtff; VF.p = A.pff; VF.q = A.qff; VF.uu = A.uuff;
-  VF.xb = A.xffb;
-  VF.vh = A.vhff; VF.SA = A.SAff; VF.SP = A.SPff; VF.Y1 = A.Y1ff; VF.Y2 = A.Y2ff; VF.twG = A.twLff;
+  // the vector sets of the three CGS precisions, CTA-uniform, kept in shared memory (passed by
+  // reference, they would otherwise be per-thread local copies)
+  __shared__ Krylov<double2> V64;
+  __shared__ Krylov<float2> V32;
+  __shared__ Krylov<ffc> VF;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    V64.x = A.x; V64.r = A.r; V64.rt = A.rt; V64.p = A.p; V64.q = A.q; V64.uu = A.uu; V64.vh = A.vh;
+    V64.xb = A.xb;
+    V64.SA = A.SA; V64.SP = A.SP; V64.Y1 = A.Y1; V64.Y2 = A.Y2; V64.twG = A.twL;
+    V32.x = A.x32; V32.r = A.r32; V32.rt = A.rt32; V32.p = A.p32; V32.q = A.q32; V32.uu = A.uu32;
+    V32.xb = A.x32b;
+    V32.vh = A.vh32; V32.SA = A.SA32; V32.SP = A.SP32; V32.Y1 = A.Y1f; V32.Y2 = A.Y2f; V32.twG = A.twL32;
+    VF.x = A.xff; VF.r = A.rff; VF.rt = A.rtff; VF.p = A.pff; VF.q = A.qff; VF.uu = A.uuff;
+    VF.xb = A.xffb;
+    VF.vh = A.vhff; VF.SA = A.SAff; VF.SP = A.SPff; VF.Y1 = A.Y1ff; VF.Y2 = A.Y2ff; VF.twG = A.twLff;
+  }
+  __syncthreads();
 
   for (int j = j0; j < j1; ++j) {
     if (j == j0 || A.lv_newsym[j]) {
@@ -1129,14 +1135,23 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
   ph_commit(A, j1 - 1);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args A, int j0, int j1) {
+// The kernels below copy their Args parameter once into shared memory: the device functions take
+// it by reference, and a reference to the parameter itself would give every thread a private
+// local-memory copy (~0.9 KB per thread, more than L1 holds for a CTA).
+__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args Ap, int j0, int j1) {
+  __shared__ Args A;
+  if (threadIdx.x == 0) A = Ap;
+  __syncthreads();
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
   march_body(A, S, j0, j1);
 }
 
 // Small instances: the same march by one CTA with block barriers only (no grid barrier cost).
-__global__ void __launch_bounds__(kThreads, 1) level_kernel_cta(Args A, int j0, int j1) {
+__global__ void __launch_bounds__(kThreads, 1) level_kernel_cta(Args Ap, int j0, int j1) {
+  __shared__ Args A;
+  if (threadIdx.x == 0) A = Ap;
+  __syncthreads();
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   cta_team_init();
   march_body(A, S, j0, j1);
@@ -1154,7 +1169,10 @@ __global__ void __launch_bounds__(kThreads, 1) history_kernel(Args A, int j) {
 // diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}, 3: A^{-1} by the Gohberg-Semencul
 // formula); x and y are padded device vectors.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args A, int op, int j, const double *xin, double *yout) {
+__global__ void __launch_bounds__(kThreads, 1) apply_kernel(Args Ap, int op, int j, const double *xin, double *yout) {
+  __shared__ Args A;
+  if (threadIdx.x == 0) A = Ap;
+  __syncthreads();
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
   const int n = A.n;
@@ -1275,7 +1293,10 @@ __device__ void setup_body(const Args &A, const SetupArgs &T, const Smem &S) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args A, SetupArgs T) {
+__global__ void __launch_bounds__(kThreads, 1) setup_kernel(Args Ap, SetupArgs T) {
+  __shared__ Args A;
+  if (threadIdx.x == 0) A = Ap;
+  __syncthreads();
   const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
   setup_body(A, T, S);
