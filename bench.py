@@ -636,6 +636,28 @@ def run_native_history(args, probs):
             uh = sh.solve()
         eh = float(np.sqrt(half.h) * np.linalg.norm(uh - half.exact(half.grid(), half.T)))
         co = {"E_M/2": eh, "E_M": errs[0], "CO_tau": math.log2(eh / errs[0])}
+    # algorithmic flops of the timed marches (level kernel roofline) and kernel time
+    flops = 0.0
+    for q, s in zip(probs, ctxs):
+        it_q, _ = s.history(q.M)
+        flops += algorithmic_flops(q, it_q, 2)
+    if args.precision == "mixed":
+        for q, st in zip(probs, stats[-1]):
+            L = max(8, 1 << math.ceil(math.log2(2 * q.n)))
+            flops += st["outer_iterations"] * (5.0 * L * math.log2(L) + 3.0 * L)
+    kernel_ms = float(sum(st["device_ms"] for st in stats[-1]))
+    launches = int(sum(st["device_launches"] for step in stats for st in step))
+    # end to end through the C ABI: H2D of u^0 and D2H of u^M per instance from pinned memory
+    import torch as _t
+    u0s = [_t.from_numpy(np.ascontiguousarray(q.phi(q.grid()))).pin_memory() for q in probs]
+    uMs = [_t.empty(q.n, dtype=_t.float64).pin_memory() for q in probs]
+    _t.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q, s, a, b in zip(probs, ctxs, u0s, uMs):
+        s.reset(u0_ptr=a.data_ptr())
+        s.solve(out_ptr=b.data_ptr())
+    _t.cuda.synchronize()
+    e2e_s = ranks.max(time.perf_counter() - t0)
     for s in ctxs:
         s.close()
     if ranks.rank != 0:
@@ -656,8 +678,17 @@ def run_native_history(args, probs):
                                  "unit": "GB/s", "frac": hbytes / (hms / 1e3) / 1e9 / peak[0],
                                  "ms": hms, "fp64_tflops": 2.0 * q0.n * jh / (hms / 1e3) / 1e12,
                                  "peak_source": peak[1]},
+            "e2e": {"value": ntot / e2e_s, "unit": "updates/s",
+                    "h2d_bytes_per_step": 8 * sum(q.n for q in probs_all),
+                    "d2h_bytes_per_step": 8 * sum(q.n for q in probs_all)},
+            "gpu_launches": launches,
+            "roofline": roofline("level_kernel", flops, kernel_ms, args.precision),
             "cgs_iterations_mean": float(np.mean(its)), "l2_error_vs_exact_at_T": errs,
             "convergence_order": co, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        v, d, cores, _ = oracle_sample(probs[0], budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                                "sample": d}
     print(json.dumps(line))
 
 
