@@ -146,6 +146,10 @@ typedef struct tsfcde_stats {
   int32_t gsf_levels;       /* IDS_CONST: levels solved by the Gohberg-Semencul formula; for
                                these, iterations count the two generator solves (level 1 only)
                                and outer_iterations the applications of A^{-1} (1 + refinements) */
+  int32_t floor_levels;     /* MIXED / IDS_CONST (info, not an error): levels whose float64
+                               residual was accepted at its floor 64 u64 kappa_eff, above tol,
+                               because refinement no longer reduced it                       */
+  int32_t pad_;
 } tsfcde_stats;
 
 /* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */

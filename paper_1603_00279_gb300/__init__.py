@@ -53,7 +53,8 @@ class Stats(C.Structure):
                 ("min_iterations", C.c_int32), ("max_residual", C.c_double),
                 ("status", C.c_int32), ("device_launches", C.c_int32),
                 ("device_ms", C.c_double), ("outer_iterations", C.c_int64),
-                ("escalated_levels", C.c_int32), ("gsf_levels", C.c_int32)]
+                ("escalated_levels", C.c_int32), ("gsf_levels", C.c_int32),
+                ("floor_levels", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

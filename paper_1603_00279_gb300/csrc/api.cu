@@ -616,7 +616,8 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
         CK(cudaMemcpy(es.data(), c->A.escalated + j0, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < nsteps; ++k) {
           stats->outer_iterations += oi[k];
-          stats->escalated_levels += es[k];
+          stats->escalated_levels += es[k] & 1;
+          stats->floor_levels += (es[k] >> 1) & 1;
         }
       }
       stats->min_iterations = it[0];

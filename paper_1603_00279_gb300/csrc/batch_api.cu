@@ -507,7 +507,8 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
           stats->max_residual = std::max(stats->max_residual, rs[x]);
           if (mixed || gsf) {
             stats->outer_iterations += oi[x];
-            stats->escalated_levels += es[x];
+            stats->escalated_levels += es[x] & 1;
+            stats->floor_levels += (es[x] >> 1) & 1;
           }
           if (gsf && j0 + k >= 1) ++stats->gsf_levels;
         }

@@ -1032,7 +1032,11 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
         if (!residual_pass(A, S, rb, [&](int m) -> double2 { return ld2(A.rt, m); }, tot)) return;
         rel = gnorm > 0.0 ? sqrt(tot[0]) / gnorm : 0.0;
         if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
-        if (rel < A.tol || rel < A.lv_floor[j]) break;
+        if (rel < A.tol) break;
+        if (rel < A.lv_floor[j]) {   // accepted at the FP64 residual floor, above tol
+          esc = 2;
+          break;
+        }
         if (outer >= 3 || (outer > 1 && rel > 0.5 * prev)) { lstat = kENotConverged; break; }
         prev = rel;
         if (!gsf_apply<true>(A, S, [&](int m, double2 z) -> double2 {
@@ -1101,7 +1105,10 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
         if (!(rel == rel) || isinf(rel)) { lstat = kENonFinite; break; }
         if (rel < A.tol) break;
         // stagnation at the FP64 residual floor (about u64 * kappa_eff) is convergence
-        if (inner_ok && rel > 0.5 * prev && rel < A.lv_floor[j]) break;
+        if (inner_ok && rel > 0.5 * prev && rel < A.lv_floor[j]) {
+          esc = 2;
+          break;
+        }
         // no progress (or diverging) in the inner precision -> finish with the FP64 CGS from x
         if (!inner_ok || rel > 0.5 * prev || outer >= A.outer_maxit) {
           esc = 1;
@@ -1117,9 +1124,10 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
     if (team().idx == 0 && threadIdx.x == 0) {
       A.iters[j] = its;
       A.resid[j] = rel;
+      // escalated[j] holds flags: bit 0 finished by the FP64 CGS, bit 1 accepted at the floor
       if (gsf) {
         A.outer_iters[j] = outer;
-        A.escalated[j] = 0;
+        A.escalated[j] = esc;
       } else if (mixed) {
         A.outer_iters[j] = outer;
         A.escalated[j] = esc;

@@ -92,3 +92,23 @@ def test_mixed_tchan_large_never_worse_than_fp64():
     b, st = _levels(P, prob, 6, precision="mixed")
     assert max(rel_l2(b[j], a[j]) for j in range(7)) <= 1e-8
     assert max(s["max_residual"] for s in st) < 1e-6
+
+
+def test_floor_flag_marks_levels_accepted_above_tol():
+    """Each mixed level either reaches tol, or is accepted at its FP64 residual floor (counted in
+    floor_levels, residual between tol and the floor), or is finished by the FP64 CGS."""
+    P = solver_module()
+    prob = W.config_mixed(M=8)              # n = 2^20 - 1
+    s = P.Solver.from_problem(prob, source="separable", precision="mixed")
+    floors = 0
+    for _ in range(4):
+        st = s.step(1)
+        assert st["floor_levels"] in (0, 1) and st["escalated_levels"] in (0, 1)
+        assert st["floor_levels"] + st["escalated_levels"] <= 1
+        if st["floor_levels"]:
+            floors += 1
+            assert 1e-12 <= st["max_residual"] < 1e-6
+        elif not st["escalated_levels"]:
+            assert st["max_residual"] < 1e-12
+    s.close()
+    assert floors >= 1   # at n = 2^20 - 1 the FP64 residual of g - A x bottoms out near 5e-9
