@@ -52,3 +52,40 @@ def test_strerror_and_version():
     assert P.strerror(0) == "ok"
     assert "converge" in P.strerror(5)
     assert b"sm_103a" in P.load_library().tsfcde_version()
+
+
+def test_invalid_options_rejected_without_device():
+    """Option checks (algorithm, precision, preconditioner, tolerances, barrier bound) come before
+    any device call, and the batch entry point checks the same options."""
+    import paper_1603_00279_gb300 as P
+    lib = P.load_library()
+    base = dict(a=0.0, b=1.0, T=1.0, N=15, M=4, alpha=0.5, beta=1.5, gamma=lambda t: 0,
+                d_plus=lambda t: 1, d_minus=lambda t: 1, phi=lambda x: x * 0)
+    bad = [dict(preconditioner="nope")]
+    for kw in bad:
+        with pytest.raises(KeyError):
+            P.Solver(**base, **kw)
+    def opt_with(**fields):
+        o = P.Options()
+        lib.tsfcde_default_options(C.byref(o))
+        for k, v in fields.items():
+            setattr(o, k, v)
+        return o
+    coef = P.COEF_FN(lambda t, u: 1.0)
+    phi = P.FIELD_FN(lambda t, x, out, n, u: None)
+    for fields in [dict(algorithm=7), dict(algorithm=-1), dict(precision=3), dict(preconditioner=5),
+                   dict(tol=0.0), dict(maxit=0), dict(barrier_spin_log2=2), dict(inner_precision=9),
+                   dict(precision=1, inner_tol=2.0)]:
+        o = opt_with(**fields)
+        ctx = C.c_void_p()
+        st = lib.tsfcde_setup(C.byref(ctx), 0.0, 1.0, 1.0, 15, 4, 0.5, 1.5, coef, coef, coef, phi,
+                              P.FIELD_FN(), None, C.byref(o))
+        assert st == 1, fields
+        assert not ctx.value
+    u0 = (C.c_double * 15)()
+    inst = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0,
+                                       C.cast(u0, C.POINTER(C.c_double))))
+    for fields in [dict(algorithm=3), dict(precision=5), dict(maxit=0)]:
+        o = opt_with(**fields)
+        h = C.c_void_p()
+        assert lib.tsfcde_batch_setup(C.byref(h), 1, inst, 4, C.byref(o)) == 1, fields
