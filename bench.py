@@ -468,7 +468,9 @@ def run_native_batch(args, probs_all):
     stream = torch.cuda.Stream()
     const = args.algorithm == "ids-const"
     b = P.Batch(probs, M, preconditioner=precond, precision=args.precision,
-                maxit=args.maxit, stream=stream.cuda_stream, algorithm=args.algorithm)
+                maxit=args.maxit, stream=stream.cuda_stream, algorithm=args.algorithm,
+                autotune=not args.no_autotune)
+    batch_plan = b.plan()
     ntot = sum(p.n for p in probs)
 
     def one_step():
@@ -533,6 +535,7 @@ def run_native_batch(args, probs_all):
                                    if ranks.world > 1 else "replicas1"),
                    "algorithm": ("IDS with constant coefficients (Gohberg-Semencul, levels >= 1)"
                                  if const else "IDS (PCGS every level)"),
+                   "launch_plan": batch_plan,
                    "updates_per_step": int(ntot_all * M),
                    "l2": "inputs larger than L2 (history %.1f GB)" % (ntot_all * M * 8 / 1e9)},
         "e2e": {"value": ntot_all * M / e2e_s, "unit": "updates/s",

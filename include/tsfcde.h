@@ -265,6 +265,14 @@ int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all);
 int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all);
 /* Release everything.  NULL is allowed. */
 void tsfcde_batch_free(tsfcde_batch *b);
+/* The batched launch's plan.  budget: complex values per shared-memory chunk (1024, 2048 or
+ * 4096; it sets the shared memory per CTA, hence the CTAs per SM); n1_ge_n2: 1 when every
+ * instance splits its half-length transform with N1 >= N2, 0 for N1 <= N2; ctas: CTAs of the
+ * launch; best_ms: the tuner's time for the first two levels of every instance (0 without
+ * tuning).  With opt->autotune = 1, tsfcde_batch_setup times every candidate on those two levels
+ * (the states then go back to level 0) and keeps the fastest; otherwise budget 2048, N1 <= N2. */
+int tsfcde_batch_get_plan(tsfcde_batch *b, int32_t *budget, int32_t *n1_ge_n2, int32_t *ctas,
+                          double *best_ms);
 
 /* The FFT plan in use: the split N/2 = N1 x N2 of the half-length transform, the per-pass chunk
  * budget (complex values per shared-memory buffer), and the autotuner's best time per operator

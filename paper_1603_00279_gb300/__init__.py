@@ -122,6 +122,9 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_batch_set_initial.argtypes = [vp, vp]
     lib.tsfcde_batch_set_initial.restype = C.c_int
     lib.tsfcde_batch_get_all.argtypes = [vp, vp]
+    lib.tsfcde_batch_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                          C.POINTER(dbl)]
+    lib.tsfcde_batch_get_plan.restype = C.c_int
     lib.tsfcde_batch_get_all.restype = C.c_int
     lib.tsfcde_batch_free.argtypes = [vp]
     lib.tsfcde_batch_free.restype = None
@@ -324,7 +327,7 @@ class Batch:
     def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
                  stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids",
-                 inner_tol: Optional[float] = None):
+                 inner_tol: Optional[float] = None, autotune: bool = False):
         self.lib = load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
@@ -348,6 +351,7 @@ class Batch:
         opt.algorithm = ALGORITHMS[algorithm]
         if inner_tol is not None:
             opt.inner_tol = inner_tol
+        opt.autotune = 1 if autotune else 0
         h = C.c_void_p()
         _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
                "tsfcde_batch_setup")
@@ -357,6 +361,15 @@ class Batch:
         s = Stats()
         _check(self.lib.tsfcde_batch_step(self.h, nsteps, C.byref(s)), "tsfcde_batch_step", True)
         return s.as_dict()
+
+    def plan(self) -> dict:
+        """The batched launch's plan (the tuner's choice when autotune was requested)."""
+        bud, big, ctas = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = C.c_double()
+        _check(self.lib.tsfcde_batch_get_plan(self.h, C.byref(bud), C.byref(big), C.byref(ctas),
+                                              C.byref(ms)), "tsfcde_batch_get_plan")
+        return {"budget": bud.value, "n1_ge_n2": bool(big.value), "ctas": ctas.value,
+                "best_ms": ms.value}
 
     def get_level(self, i: int):
         out = np.empty(self.n[i])

@@ -260,12 +260,10 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   if (c->smem > prop.sharedMemPerBlockOptin) return TSFCDE_E_INVALID_ARG;
   const size_t smem_limit = prop.sharedMemPerBlockOptin;
   {
-    // the attribute covers every plan the autotuner may try
-    const size_t smax = std::min(smem_limit, (size_t)(2 * 4096 + 4096) * sizeof(double2) + 4096);
+    // the limit covers every plan the autotuner may try and every other context
     for (const void *fn : {tsf::level_kernel_ptr(), tsf::apply_kernel_ptr(), tsf::setup_kernel_ptr(),
-                           tsf::history_kernel_ptr()}) {
-      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)std::max(smax, c->smem)));
+                           tsf::history_kernel_ptr(), tsf::level_kernel_cta_ptr()}) {
+      if (tsf::raise_smem_limit(fn, prop) < c->smem) return TSFCDE_E_INVALID_ARG;
       int occ = 0;
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
       if (occ < 1) return TSFCDE_E_INVALID_ARG;
@@ -492,8 +490,6 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     set_caps(B, 1, c->budget);
     c->smem_cta = tsf::level_smem_bytes(B);
     if (c->smem_cta > smem_limit) return TSFCDE_E_INVALID_ARG;
-    CK(cudaFuncSetAttribute(tsf::level_kernel_cta_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)c->smem_cta));
   }
   c->level = 0;
   return TSFCDE_OK;

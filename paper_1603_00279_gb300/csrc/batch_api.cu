@@ -38,6 +38,10 @@ struct tsfcde_batch {
   size_t u_total = 0;
   int grid = 0;
   size_t smem = 0;
+  int grid_alloc = 0;                // CTAs given per-CTA scratch (the largest launch)
+  int budget = 2048;                 // plan: chunk budget and split orientation (autotuner's)
+  bool n1_large = false;
+  double tune_best_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -72,13 +76,15 @@ struct Carver {
   }
 };
 
-void plan(Args &A, int64_t n) {
+// Plan of one instance: FFT sizes, the four-step split of the half-length transform (N1 <= N2,
+// or N1 >= N2 when n1_large) and per-pass chunks of at most `budget` complex values.
+void plan(Args &A, int64_t n, int budget = 2048, bool n1_large = false) {
   const int lgL = std::max(3, ilog2(2 * n));
   A.cp.lgL = lgL;
   A.cp.L = 1 << lgL;
   A.cp.lgN = lgL - 1;
   A.cp.N = 1 << A.cp.lgN;
-  A.cp.lg1 = A.cp.lgN / 2;
+  A.cp.lg1 = n1_large ? A.cp.lgN - A.cp.lgN / 2 : A.cp.lgN / 2;
   A.cp.lg2 = A.cp.lgN - A.cp.lg1;
   A.cp.N1 = 1 << A.cp.lg1;
   A.cp.N2 = 1 << A.cp.lg2;
@@ -89,7 +95,6 @@ void plan(Args &A, int64_t n) {
   A.bp.N1 = 1 << A.bp.lg1;
   A.bp.N2 = 1 << A.bp.lg2;
   // one-CTA team: every item of a pass belongs to the CTA, processed in chunks
-  const int budget = 2048;
   auto cap = [&](int items, int lines_per_item, int lg) {
     return std::max(1, std::min(items, std::max(1, (budget >> lg) / lines_per_item)));
   };
@@ -113,6 +118,111 @@ void tsfcde_batch_free(tsfcde_batch *b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->stream && b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
+}
+
+static tsf::BatchArgs batch_args(const tsfcde_batch *b) {
+  tsf::BatchArgs B;
+  B.count = (int)b->count;
+  B.inst = b->d_inst;
+  B.setup = b->d_setup;
+  B.cta = b->d_cta;
+  B.order = b->d_order;
+  B.next = b->d_next;
+  return B;
+}
+
+// Worst per-instance status after a launch (the first non-OK one that is not NOT_CONVERGED, else
+// NOT_CONVERGED if any, else OK); a CUDA error code when the copy fails.
+static int batch_status(tsfcde_batch *b) {
+  std::vector<int> h((size_t)b->count * 4);
+  CK(cudaMemcpy(h.data(), b->d_status, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  int worst = TSFCDE_OK;
+  for (int64_t i = 0; i < b->count; ++i) {
+    const int hi = h[(size_t)i * 4];
+    if (hi && hi != TSFCDE_E_NOT_CONVERGED) return hi;
+    if (hi) worst = hi;
+  }
+  return worst;
+}
+
+// Per-instance tables and spectra on the device (they depend on the plan's split).
+static int batch_device_setup(tsfcde_batch *b) {
+  CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->count * 4 * sizeof(int), b->stream));
+  CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
+  const int st = tsf::launch_batch(batch_args(b), b->grid, b->smem, b->stream, 1, 0, 0);
+  if (st) return st;
+  CK(cudaStreamSynchronize(b->stream));
+  return batch_status(b);
+}
+
+// Every instance's plan for a chunk budget and split orientation; the launch shape follows
+// (CTAs per SM from the occupancy at that shared memory, never more than were given scratch).
+static int batch_apply_plan(tsfcde_batch *b, const tsfcde_instance *in, const cudaDeviceProp &prop,
+                            int budget, bool n1_large, bool *usable) {
+  size_t smax = 0;
+  for (int64_t i = 0; i < b->count; ++i) {
+    plan(b->inst[i], in[i].N, budget, n1_large);
+    smax = std::max(smax, tsf::level_smem_bytes(b->inst[i]));
+  }
+  int occ = 0, occ2 = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tsf::batch_level_kernel_ptr(), tsf::kThreads, smax));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, tsf::batch_setup_kernel_ptr(), tsf::kThreads, smax));
+  *usable = occ >= 1 && occ2 >= 1;
+  if (!*usable) return TSFCDE_OK;
+  b->smem = smax;
+  b->grid = std::min(b->grid_alloc, std::min(occ, occ2) * prop.multiProcessorCount);
+  b->budget = budget;
+  b->n1_large = n1_large;
+  CK(cudaMemcpyAsync(b->d_inst, b->inst.data(), b->count * sizeof(Args), cudaMemcpyHostToDevice, b->stream));
+  return TSFCDE_OK;
+}
+
+// Setup-time tuner of the batched launch: chunk budgets of 1024, 2048 and 4096 complex values
+// (shared memory per CTA, hence CTAs per SM) times the two split orientations, each timed on
+// the first two levels of every instance with its own spectra; the fastest is kept and the
+// states go back to level 0.
+static int batch_autotune(tsfcde_batch *b, const tsfcde_instance *in, const cudaDeviceProp &prop) {
+  bool any_odd = false;
+  for (int64_t i = 0; i < b->count; ++i) any_odd = any_odd || (b->inst[i].cp.lgN & 1);
+  const int nlev = (int)std::min<int64_t>(b->M, 2);
+  float best = 1e30f;
+  int best_budget = b->budget;
+  bool best_large = b->n1_large;
+  for (int budget : {1024, 2048, 4096}) {
+    for (bool large : {false, true}) {
+      if (large && !any_odd) continue;   // the same split for every instance
+      bool usable = false;
+      int st = batch_apply_plan(b, in, prop, budget, large, &usable);
+      if (st) return st;
+      if (!usable) continue;
+      st = batch_device_setup(b);
+      if (st) return st;
+      st = tsfcde_batch_reset(b);
+      if (st) return st;
+      CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->count * 4 * sizeof(int), b->stream));
+      CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
+      CK(cudaEventRecord(b->ev0, b->stream));
+      st = tsf::launch_batch(batch_args(b), b->grid, b->smem, b->stream, 0, 0, nlev);
+      if (st) return st;
+      CK(cudaEventRecord(b->ev1, b->stream));
+      CK(cudaStreamSynchronize(b->stream));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+      st = batch_status(b);
+      if (st != TSFCDE_OK && st != TSFCDE_E_NOT_CONVERGED) return st;
+      if (ms < best) {
+        best = ms;
+        best_budget = budget;
+        best_large = large;
+      }
+    }
+  }
+  bool usable = false;
+  int st = batch_apply_plan(b, in, prop, best_budget, best_large, &usable);
+  if (st) return st;
+  if (!usable) return TSFCDE_E_INVALID_ARG;
+  b->tune_best_ms = best;
+  return batch_device_setup(b);
 }
 
 static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
@@ -151,9 +261,8 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     smax = std::max(smax, tsf::level_smem_bytes(A));
   }
   b->smem = smax;
-  if (b->smem > prop.sharedMemPerBlockOptin) return TSFCDE_E_INVALID_ARG;
   for (const void *fn : {tsf::batch_level_kernel_ptr(), tsf::batch_setup_kernel_ptr()}) {
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    if (tsf::raise_smem_limit(fn, prop) < b->smem) return TSFCDE_E_INVALID_ARG;
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, b->smem));
     if (occ < 1) return TSFCDE_E_INVALID_ARG;
@@ -339,23 +448,13 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
                        cudaMemcpyHostToDevice, b->stream));
   }
   CK(cudaStreamSynchronize(b->stream));
-  // ---- device setup: weights, tables, spectra of every instance ----
-  tsf::BatchArgs B;
-  B.count = (int)K;
-  B.inst = b->d_inst;
-  B.setup = b->d_setup;
-  B.cta = b->d_cta;
-  B.order = b->d_order;
-  B.next = b->d_next;
-  CK(cudaMemsetAsync(b->d_next, 0, 256, b->stream));
-  int st = tsf::launch_batch(B, b->grid, b->smem, b->stream, 1, 0, 0);
+  // ---- device setup: weights, tables, spectra of every instance; then the plan tuner ----
+  b->grid_alloc = b->grid;
+  int st = batch_device_setup(b);
   if (st) return st;
-  CK(cudaStreamSynchronize(b->stream));
-  {
-    std::vector<int> h((size_t)K * 4);
-    CK(cudaMemcpy(h.data(), b->d_status, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int64_t i = 0; i < K; ++i)
-      if (h[(size_t)i * 4]) return h[(size_t)i * 4];
+  if (b->opt.autotune) {
+    st = batch_autotune(b, in, prop);
+    if (st) return st;
   }
   return tsfcde_batch_reset(b);
 }
@@ -428,6 +527,16 @@ int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all) {
   CK(cudaSetDevice(b->device));
   CK(cudaMemcpyAsync(b->d_u0, u0_all, b->u_total * sizeof(double), cudaMemcpyHostToDevice, b->stream));
   return tsfcde_batch_reset(b);
+}
+
+int tsfcde_batch_get_plan(tsfcde_batch *b, int32_t *budget, int32_t *n1_ge_n2, int32_t *ctas,
+                          double *best_ms) {
+  if (!b) return TSFCDE_E_INVALID_ARG;
+  if (budget) *budget = b->budget;
+  if (n1_ge_n2) *n1_ge_n2 = b->n1_large ? 1 : 0;
+  if (ctas) *ctas = b->grid;
+  if (best_ms) *best_ms = b->tune_best_ms;
+  return TSFCDE_OK;
 }
 
 int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all) {

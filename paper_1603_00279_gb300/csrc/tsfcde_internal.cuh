@@ -476,6 +476,19 @@ struct BatchArgs {
   unsigned *next;              // work-queue counter (zeroed before each launch)
 };
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum (minus its static shared
+// memory).  The limit is a per-function, process-wide attribute: setting it to one context's
+// need would break another context that needs more; occupancy depends only on what each launch
+// requests.  Returns the usable dynamic bytes, or 0 on a CUDA error.
+inline size_t raise_smem_limit(const void *fn, const cudaDeviceProp &prop) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
+  const size_t dyn = prop.sharedMemPerBlockOptin > fa.sharedSizeBytes
+                         ? prop.sharedMemPerBlockOptin - fa.sharedSizeBytes : 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return 0;
+  return dyn;
+}
+
 // Host-side entry points implemented in level_kernels.cu.
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,

@@ -54,3 +54,20 @@ def test_batch_reset_and_tchan():
         b.step(6)
         for i in range(len(probs)):
             assert rel_l2(b.get_level(i)[0], refs[i][6]) <= 1e-10
+
+
+@pytest.mark.parametrize("algorithm", ["ids", "ids-const"])
+def test_autotuned_batch_plan_matches_oracle(algorithm):
+    """The batch plan tuner tries chunk budgets and split orientations on the first two levels;
+    the states then restart from level 0 and the march with the kept plan matches elimination."""
+    P = solver_module()
+    probs = W.config_batch(count=12, M=6, seed=7, n_lo=200, n_hi=2100)
+    b = P.Batch(probs, 6, algorithm=algorithm, autotune=True)
+    plan = b.plan()
+    assert plan["budget"] in (1024, 2048, 4096) and plan["best_ms"] > 0 and plan["ctas"] >= 152
+    assert b.get_level(0)[1] == 0
+    b.step(6)
+    for i, q in enumerate(probs):
+        ref = O.run(q)
+        assert rel_l2(b.get_level(i)[0], ref[-1]) <= 1e-10, (i, q.n)
+    b.close()
