@@ -154,3 +154,24 @@ def test_const_batch_matches_oracle():
         ref = O.run(p)
         assert rel_l2(b.get_level(i)[0], ref[-1]) <= 1e-10, i
     b.close()
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_const_shortest_marches(M):
+    """M = 1 has no level j >= 1 (plain CGS only); M = 2 builds the generators for its single
+    Gohberg-Semencul level; M = 3 uses them once more."""
+    P = solver_module()
+    prob = _batch_instance(300, M, idx=1)
+    ref = O.run(prob)
+    s = P.Solver.from_problem(prob, algorithm="ids-const")
+    st = s.step(M)
+    assert st["gsf_levels"] == M - 1
+    assert rel_l2(s.get_level()[0], ref[-1]) <= 1e-10
+    s.close()
+    probs = W.config_batch(count=3, M=M, seed=9, n_lo=100, n_hi=400)
+    b = P.Batch(probs, M, algorithm="ids-const")
+    st = b.step(M)
+    assert st["gsf_levels"] == 3 * (M - 1)
+    for i, q in enumerate(probs):
+        assert rel_l2(b.get_level(i)[0], O.run(q)[-1]) <= 1e-10
+    b.close()
