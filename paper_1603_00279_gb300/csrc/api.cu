@@ -42,6 +42,7 @@ struct tsfcde_ctx {
   int march_grid = 0;   // CTAs of the level-march launch (1: one-CTA team for small N)
   bool gsf_ready = false;   // Gohberg-Semencul generators built (a march passed level 1)
   size_t smem_cta = 0;      // dynamic shared memory of the one-CTA march for the final plan
+  int march_threads = 256;  // threads per CTA of the whole-grid march
 };
 
 namespace {
@@ -267,6 +268,16 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
       int occ = 0;
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tsf::kThreads, c->smem));
       if (occ < 1) return TSFCDE_E_INVALID_ARG;
+    }
+    // large FFT half-lengths march with 512 threads per CTA (more warps to cover the memory
+    // latency of their L2-spilling work arrays); measured faster from N = 2^19 on, slower below
+    c->march_threads = A.cp.lgN >= tsf::kWideMinLgN ? tsf::kWideThreads : tsf::kThreads;
+    if (c->march_threads == tsf::kWideThreads) {
+      if (tsf::raise_smem_limit(tsf::level_kernel_wide_ptr(), prop) < c->smem) return TSFCDE_E_INVALID_ARG;
+      int occ = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tsf::level_kernel_wide_ptr(), tsf::kWideThreads,
+                                                       c->smem));
+      if (occ < 1) c->march_threads = tsf::kThreads;
     }
   }
 
@@ -575,7 +586,7 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
       set_caps(B, 1, c->budget);
       st = tsf::launch_levels(B, 1, c->smem_cta, c->stream, (int)s, (int)e);
     } else {
-      st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e);
+      st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e, c->march_threads);
     }
     c->A.test_skip = 0;   // the testing hook applies to one launch only
     if (st) return st;

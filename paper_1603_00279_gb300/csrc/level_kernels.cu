@@ -1146,7 +1146,8 @@ __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) {
 // The kernels below copy their Args parameter once into shared memory: the device functions take
 // it by reference, and a reference to the parameter itself would give every thread a private
 // local-memory copy (~0.9 KB per thread, more than L1 holds for a CTA).
-__global__ void __launch_bounds__(kThreads, 1) level_kernel(Args Ap, int j0, int j1) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) level_kernel(Args Ap, int j0, int j1) {
   __shared__ Args A;
   if (threadIdx.x == 0) A = Ap;
   __syncthreads();
@@ -1499,9 +1500,12 @@ __global__ void time_tables_kernel(int M, double alpha, double tau, double h, do
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-static int coop_launch(const void *fn, int grid, size_t smem, cudaStream_t st, void **args) {
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kThreads, args, smem, st);
+static int coop_launch_n(const void *fn, int grid, int threads, size_t smem, cudaStream_t st, void **args) {
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, threads, args, smem, st);
   return e == cudaSuccess ? kOK : kECuda;
+}
+static int coop_launch(const void *fn, int grid, size_t smem, cudaStream_t st, void **args) {
+  return coop_launch_n(fn, grid, kThreads, smem, st, args);
 }
 
 size_t level_smem_bytes(const Args &A) {
@@ -1515,7 +1519,8 @@ size_t level_smem_bytes(const Args &A) {
   return (size_t)(2 * m + (1 << lt)) * sizeof(double2) + 4 * 32 * sizeof(double);
 }
 
-const void *level_kernel_ptr() { return (const void *)level_kernel; }
+const void *level_kernel_ptr() { return (const void *)level_kernel<kThreads>; }
+const void *level_kernel_wide_ptr() { return (const void *)level_kernel<kWideThreads>; }
 const void *history_kernel_ptr() { return (const void *)history_kernel; }
 
 int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j) {
@@ -1536,14 +1541,16 @@ int launch_batch(const BatchArgs &B, int grid, size_t smem, cudaStream_t st, int
 const void *apply_kernel_ptr() { return (const void *)apply_kernel; }
 const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
 
-int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1) {
+int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1, int threads) {
   Args a = A;
   if (grid == 1) {   // one-CTA team
     level_kernel_cta<<<1, kThreads, smem, st>>>(a, j0, j1);
     return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
   }
   void *args[] = {&a, &j0, &j1};
-  return coop_launch((const void *)level_kernel, grid, smem, st, args);
+  if (threads == kWideThreads)
+    return coop_launch_n((const void *)level_kernel<kWideThreads>, grid, kWideThreads, smem, st, args);
+  return coop_launch_n((const void *)level_kernel<kThreads>, grid, kThreads, smem, st, args);
 }
 const void *level_kernel_cta_ptr() { return (const void *)level_kernel_cta; }
 

@@ -20,7 +20,9 @@
 
 namespace tsf {
 
-constexpr int kThreads = 256;                 // threads per CTA of every kernel
+constexpr int kThreads = 256;                 // threads per CTA of every kernel but one:
+constexpr int kWideThreads = 512;             // the whole-grid level march for FFT half-lengths
+constexpr int kWideMinLgN = 19;               // N >= 2^19 (more warps to cover memory latency)
 constexpr long long kSpinLimit = 1ll << 23;   // default bound on a barrier wait (a few seconds)
 
 // status codes (mirror include/tsfcde.h)
@@ -490,7 +492,8 @@ inline size_t raise_smem_limit(const void *fn, const cudaDeviceProp &prop) {
 }
 
 // Host-side entry points implemented in level_kernels.cu.
-int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
+int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1,
+                  int threads = kThreads);
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
                  const double *xin, double *yout);
 int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const double *omega,
@@ -503,6 +506,7 @@ int launch_time_tables(int M, double alpha, double tau, double h, double beta, c
 size_t level_smem_bytes(const Args &A);
 const void *level_kernel_ptr();
 const void *level_kernel_cta_ptr();
+const void *level_kernel_wide_ptr();
 const void *history_kernel_ptr();
 int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j);
 const void *batch_level_kernel_ptr();
