@@ -161,3 +161,24 @@ def test_history_workload_full_size():
     _, rs = s.history(LEVELS)
     s.close()
     _check_levels(prob, levels, rs, seed=3, label="history n=262143")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_largest_supported_n(precision):
+    """N = 2^22 - 1, the largest the ABI accepts (FFT half-length 2^22, 4096-point Bluestein rows,
+    about 193 KB of shared memory per CTA, 512 threads per CTA): 3 levels of the small workload's
+    coefficients against the row-wise level equations and the manufactured solution."""
+    P = solver_module()
+    prob = W.config_small(n=(1 << 22) - 1, M=3)
+    s = P.Solver.from_problem(prob, source="separable", precision=precision)
+    levels = _march_levels(s, prob.M)
+    _, rs = s.history(prob.M)
+    s.close()
+    _check_levels(prob, levels, rs, seed=4, label=f"n=2^22-1 {precision}")
+    # at tau = 1/3 the scheme's time error dominates and hardly depends on n: the error against
+    # the manufactured solution equals the oracle's at n = 1023 (0.01154; h^2 terms move it by
+    # about 3e-6 from there)
+    small = W.config_small(n=1023, M=3)
+    e_ref = rel_l2(O.run(small)[-1], small.exact(small.grid(), small.T))
+    e_gpu = rel_l2(levels[-1], prob.exact(prob.grid(), prob.T))
+    assert abs(e_gpu - e_ref) < 5e-5, (e_gpu, e_ref)
