@@ -5,12 +5,21 @@ A step is one whole time march of the workload (all M levels: history sum, FFT T
 products, circulant-preconditioned CGS per level) from u^0, inputs resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--workload large|small|mixed] [--precond tchan|strang|none]
+                    [--workload large|small|mixed|batch|history] [--precond tchan|strang|none]
+                    [--precision fp64|mixed] [--algorithm ids|ids-const] [--instances K]
+                    [--no-autotune] [--no-cpu-baseline] [--co]
 
 Default workload: n = 2^16-1 interior points, M = 1024 levels, alpha = 0.3, beta = 1.9,
 gamma = 0.5, d+ = 1+t, d- = 1-t/2, u = (t^2+1) x^2 (1-x)^2, T. Chan preconditioner, tol 1e-12,
-FP64.  Multi-GPU (torchrun): independent replicas, one per rank (the march is sequential in
-time and a single instance does not shard), weak scaling, max time over ranks.
+FP64.  Other workloads: small (n = 127, M = 64, Strang), mixed (n = 2^20-1, M = 512, mixed
+precision by default), batch (4096 constant-coefficient instances, M = 256; --algorithm
+ids-const applies A^{-1} by the Gohberg-Semencul formula for j >= 1), history (n = 2^18-1,
+M = 8192, mixed precision with FP64 history; --co adds the convergence order in tau).
+
+Multi-GPU (torchrun): one instance runs as independent replicas, one per rank (the march is
+sequential in time and a single instance does not shard; weak scaling); the batch and history
+workloads shard their instances over the ranks by estimated cost (strong scaling).  The step
+time is the slowest rank's.
 
 --impl reference times the FP64 CPU oracle (dense Gaussian elimination per level) on the host
 cores, on a bounded sample of the same workload.
