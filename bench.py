@@ -335,9 +335,11 @@ def run_native(args, p):
     import paper_1603_00279_gb300 as P
 
     stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
     s = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
                               maxit=args.maxit, precision=args.precision,
                               autotune=not args.no_autotune)
+    setup_ms = 1e3 * (time.perf_counter() - t_setup)
     plan = s.plan()
     n, M = p.n, p.M
 
@@ -439,6 +441,7 @@ def run_native(args, p):
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
+        "setup_ms": setup_ms,
         "roofline": roofline("level_kernel", flops, kernel_ms, args.precision),
         "history_roofline": hist,
         "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max()),
@@ -476,9 +479,11 @@ def run_native_batch(args, probs_all):
     precond = args.precond or "strang"
     stream = torch.cuda.Stream()
     const = args.algorithm == "ids-const"
+    t_setup = time.perf_counter()
     b = P.Batch(probs, M, preconditioner=precond, precision=args.precision,
                 maxit=args.maxit, stream=stream.cuda_stream, algorithm=args.algorithm,
                 autotune=not args.no_autotune)
+    setup_ms = 1e3 * (time.perf_counter() - t_setup)
     batch_plan = b.plan()
     ntot = sum(p.n for p in probs)
 
@@ -550,6 +555,7 @@ def run_native_batch(args, probs_all):
         "e2e": {"value": ntot_all * M / e2e_s, "unit": "updates/s",
                 "h2d_bytes_per_step": 8 * int(ntot_all), "d2h_bytes_per_step": 8 * int(ntot_all)},
         "gpu_launches": int(sum(st["device_launches"] for st in stats)),
+        "setup_ms": setup_ms,
         "roofline": roofline("batch_level_kernel", flops, kernel_ms, args.precision),
         "cgs_iterations": {"mean": float(its_all.mean()), "min": int(its_all.min()),
                            "max": int(its_all.max()),

@@ -263,6 +263,10 @@ int tsfcde_batch_reset(tsfcde_batch *b);
 int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all);
 /* Copy every instance's current level to u_all (host, concatenated like u0_all). */
 int tsfcde_batch_get_all(tsfcde_batch *b, double *u_all);
+/* Advance every instance to level M (tsfcde_batch_step) and copy every u^M to u_all (host,
+ * concatenated like u0_all; NULL skips the copy).  Returns the step's status; the copy is made
+ * after E_NOT_CONVERGED too. */
+int tsfcde_batch_solve(tsfcde_batch *b, double *u_all, tsfcde_stats *stats);
 /* Release everything.  NULL is allowed. */
 void tsfcde_batch_free(tsfcde_batch *b);
 /* The batched launch's plan.  budget: complex values per shared-memory chunk (1024, 2048 or

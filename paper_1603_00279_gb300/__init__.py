@@ -122,6 +122,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_batch_set_initial.argtypes = [vp, vp]
     lib.tsfcde_batch_set_initial.restype = C.c_int
     lib.tsfcde_batch_get_all.argtypes = [vp, vp]
+    lib.tsfcde_batch_solve.argtypes = [vp, vp, C.POINTER(Stats)]
+    lib.tsfcde_batch_solve.restype = C.c_int
     lib.tsfcde_batch_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                           C.POINTER(dbl)]
     lib.tsfcde_batch_get_plan.restype = C.c_int
@@ -361,6 +363,18 @@ class Batch:
         s = Stats()
         _check(self.lib.tsfcde_batch_step(self.h, nsteps, C.byref(s)), "tsfcde_batch_step", True)
         return s.as_dict()
+
+    def solve(self) -> list:
+        """Advance every instance to level M; returns the list of u^M (numpy arrays)."""
+        st = Stats()
+        out = np.empty(sum(self.n))
+        _check(self.lib.tsfcde_batch_solve(self.h, _dptr(out), C.byref(st)), "tsfcde_batch_solve", True)
+        self.last_stats = st.as_dict()
+        parts, k = [], 0
+        for n in self.n:
+            parts.append(out[k:k + n].copy())
+            k += n
+        return parts
 
     def plan(self) -> dict:
         """The batched launch's plan (the tuner's choice when autotune was requested)."""

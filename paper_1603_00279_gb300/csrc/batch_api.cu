@@ -529,6 +529,17 @@ int tsfcde_batch_set_initial(tsfcde_batch *b, const double *u0_all) {
   return tsfcde_batch_reset(b);
 }
 
+int tsfcde_batch_solve(tsfcde_batch *b, double *u_all, tsfcde_stats *stats) {
+  if (!b) return TSFCDE_E_INVALID_ARG;
+  const int st = tsfcde_batch_step(b, b->M - b->level, stats);
+  if (st != TSFCDE_OK && st != TSFCDE_E_NOT_CONVERGED) return st;
+  if (u_all) {
+    const int st2 = tsfcde_batch_get_all(b, u_all);
+    if (st2) return st2;
+  }
+  return st;
+}
+
 int tsfcde_batch_get_plan(tsfcde_batch *b, int32_t *budget, int32_t *n1_ge_n2, int32_t *ctas,
                           double *best_ms) {
   if (!b) return TSFCDE_E_INVALID_ARG;

@@ -97,3 +97,17 @@ def test_contexts_of_different_sizes_coexist():
     assert rel_l2(s1.get_level()[0], O.run(W.config_small(n=255, M=3))[-1]) <= 1e-10
     for o in (b1, b2, s1, s2):
         o.close()
+
+
+def test_batch_solve_equals_step_and_get():
+    P = solver_module()
+    probs = W.config_batch(count=5, M=6, n_lo=255, n_hi=1100)
+    b = P.Batch(probs, 6)
+    u = b.solve()
+    assert b.last_stats["level"] == 6 and len(u) == len(probs)
+    b.reset()
+    b.step(6)
+    for i in range(len(probs)):
+        assert np.array_equal(u[i], b.get_level(i)[0])
+        assert rel_l2(u[i], O.run(probs[i])[-1]) <= 1e-10
+    b.close()
