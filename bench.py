@@ -254,6 +254,32 @@ def oracle_sample(p, budget_s: float = 15.0):
     return n_s * levels / dt, desc, cores, dt
 
 
+def oracle_single_core(p):
+    """One level of the oracle at the sample size on one core (BLAS limited to one thread in a
+    child process), in updates/s, or None if the child fails."""
+    n_s = min(p.n, 2047)
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import oracle as O, tsfcde_workloads as W\n"
+        f"name = {p.name!r}\n"
+        f"n_s, M = {n_s}, {p.M}\n"
+        "if name.startswith('history'):\n"
+        "    q = W.config_history(n=n_s, M=M)[int(name[7:])]\n"
+        "else:\n"
+        "    q = {'large': W.config_large, 'small': W.config_small, 'mixed': W.config_mixed}[name](n=n_s, M=M)\n"
+        "t0 = time.perf_counter(); O.run(q, levels=1); dt = time.perf_counter() - t0\n"
+        "print(json.dumps(n_s / dt))\n")
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=120)
+        return {"value": float(r.stdout.strip().splitlines()[-1]), "unit": "updates/s", "cores": 1,
+                "sample": f"one level at n={n_s}"}
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
+
+
 def run_reference(args, p):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -456,7 +482,7 @@ def run_native(args, p):
     if not args.no_cpu_baseline and world == 1:
         v, d, cores, _ = oracle_sample(p, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
-                                "sample": d}
+                                "sample": d, "single_core": oracle_single_core(p)}
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
