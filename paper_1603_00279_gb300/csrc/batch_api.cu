@@ -114,6 +114,11 @@ void tsfcde_batch_free(tsfcde_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->arena) cudaFree(b->arena);
   if (b->scratch) cudaFree(b->scratch);
+  if (b->d_inst) cudaFree(b->d_inst);
+  if (b->d_setup) cudaFree(b->d_setup);
+  if (b->d_cta) cudaFree(b->d_cta);
+  if (b->d_order) cudaFree(b->d_order);
+  if (b->d_next) cudaFree(b->d_next);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->stream && b->own_stream) cudaStreamDestroy(b->stream);

@@ -111,3 +111,25 @@ def test_batch_solve_equals_step_and_get():
         assert np.array_equal(u[i], b.get_level(i)[0])
         assert rel_l2(u[i], O.run(probs[i])[-1]) <= 1e-10
     b.close()
+
+
+def test_contexts_release_device_memory():
+    """Creating and freeing contexts and batches returns their device memory."""
+    torch = pytest.importorskip("torch")
+    P = solver_module()
+    probs = W.config_batch(count=64, M=4, n_lo=255, n_hi=4095)
+    # warm: library load, kernel modules and the first allocations of the process
+    P.Batch(probs, 4).close()
+    P.Solver.from_problem(W.config_small(n=65535, M=4)).close()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(8):
+        b = P.Batch(probs, 4)
+        b.step(2)
+        b.close()
+        s = P.Solver.from_problem(W.config_small(n=65535, M=4))
+        s.step(2)
+        s.close()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (16 << 20), (free0 - free1) / 2**20
