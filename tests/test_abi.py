@@ -89,3 +89,27 @@ def test_invalid_options_rejected_without_device():
         o = opt_with(**fields)
         h = C.c_void_p()
         assert lib.tsfcde_batch_setup(C.byref(h), 1, inst, 4, C.byref(o)) == 1, fields
+
+
+def test_header_is_c99_and_links():
+    """A plain C99 program compiled against include/tsfcde.h and linked to libtsfcde.so calls the
+    entry points that need no device (defaults, strerror, version, argument checks, NULL frees)."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1603_00279_gb300 import build
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "abi_c_check")
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror",
+                            "-I", os.path.join(ROOT, "include"),
+                            os.path.join(ROOT, "tests", "abi_c_check.c"), "-o", exe,
+                            "-L", libdir, "-ltsfcde", "-Wl,-rpath," + libdir],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+        assert r.returncode == 0 and "c abi ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
