@@ -494,6 +494,8 @@ inline size_t raise_smem_limit(const void *fn, const cudaDeviceProp &prop) {
 // Host-side entry points implemented in level_kernels.cu.
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1,
                   int threads = kThreads);
+int launch_levels_wide(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
+int launch_levels_cta(const Args &A, size_t smem, cudaStream_t st, int j0, int j1);
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
                  const double *xin, double *yout);
 int launch_setup(const Args &A, int grid, size_t smem, cudaStream_t st, const double *omega,
