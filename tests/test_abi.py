@@ -113,3 +113,23 @@ def test_header_is_c99_and_links():
         assert r.returncode == 0, r.stderr
         r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
         assert r.returncode == 0 and "c abi ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+def test_product_never_uses_the_oracle():
+    """The package (binding, build, host helpers and CUDA sources) neither imports nor names the
+    oracle: the product path is the CUDA library alone."""
+    pkg = os.path.join(ROOT, "paper_1603_00279_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_lib" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+                assert "ids_oracle" not in src, f
+
+
+def test_binding_fails_loudly_without_the_library():
+    import paper_1603_00279_gb300 as P
+    with pytest.raises(RuntimeError):
+        P.load_library(os.path.join(ROOT, "paper_1603_00279_gb300", "_lib", "missing.so"))
