@@ -353,7 +353,7 @@ def l2_norm(v: np.ndarray, h: float) -> float:
 
 
 def errors_vs_exact(prob, levels: List[np.ndarray]):
-    """max_n ||E^n||_0 and max |E| over the grid (Section 4, Tables 1-8)."""
+    """max_n ||E^n||_0 and max |E| over the grid (Section 4, Tables 1, 2, 5 and 6)."""
     x = prob.grid()
     e2, emax = 0.0, 0.0
     for j, u in enumerate(levels):

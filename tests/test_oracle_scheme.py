@@ -24,7 +24,7 @@ def _rows():
 
 @pytest.mark.parametrize("row", _rows(), ids=lambda r: f"{r[0]}-a{r[1]}-h{r[3]}")
 def test_paper_error_tables(row):
-    """Tables 1 and 7 (Section 4): max_n ||E^n||_0 and max|E| at tau = h."""
+    """Tables 1 and 5 (Section 4): max_n ||E^n||_0 and max|E| at tau = h."""
     ex, alpha, beta, hinv, e2_ref, em_ref = row
     make = W.example1 if ex == "ex1" else W.example2
     p = make(hinv - 1, hinv, alpha, beta)
