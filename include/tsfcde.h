@@ -104,11 +104,11 @@ typedef struct tsfcde_options {
  *   circulant-preconditioned CGS.
  * TSFCDE_ALG_IDS_CONST: Algorithm "Practical implementation of IDS with constant coefficients"
  *   (Section 3.2), for gamma, d_+ and d_- constant in t.  Then A^{(j+sigma)} = A for every
- *   j >= 1 (Eq. (3.4) context).  Level 0 is solved by CGS as usual.  At level 1 the two systems
- *   A x = e_1 and A y = e_N of Eq. (3.4) are solved by the preconditioned CGS, each refined once
+ *   j >= 1 (Eq. (3.4)).  Level 0 is solved by CGS as usual.  At level 1 the two systems
+ *   A x = e_1 and A y = e_N of Eq. (3.5) are solved by the preconditioned CGS, each refined once
  *   with the inverse they define.  Every level j >= 1 then computes u^{j+1} = A^{-1} g by the
- *   Gohberg-Semencul formula: Algorithm "Compute z = A^{-1} v", four triangular Toeplitz products
- *   by FFT, with no Krylov iterations.  The level's FP64 residual ||g - A u^{j+1}|| / ||g|| is
+ *   Gohberg-Semencul formula (Eq. (3.6), Section 3.1): Algorithm "Compute z = A^{-1} v", four
+ *   triangular Toeplitz products by FFT, with no Krylov iterations.  The level's FP64 residual ||g - A u^{j+1}|| / ||g|| is
  *   measured.  While it is above both tol and 64 u64 kappa_eff, the level is refined,
  *   u += A^{-1}(g - A u), at most twice.  A level still above both is reported as
  *   TSFCDE_E_NOT_CONVERGED with its state kept.

@@ -16,8 +16,8 @@ do not feed the level solutions.
 
 For constant coefficients (Section 3.2) `run_const` follows Algorithm "Practical implementation of
 IDS with constant coefficients": level 0 by elimination, every later level by the Gohberg-Semencul
-formula (after Eq. (3.4)) applied as in Algorithm "Compute z = A^{-1} v", with the two generator
-systems of Eq. (3.4) solved by elimination and the four triangular Toeplitz factors formed densely.
+formula (Eq. (3.6)) applied as in Algorithm "Compute z = A^{-1} v", with the two generator
+systems of Eq. (3.5) solved by elimination and the four triangular Toeplitz factors formed densely.
 It reaches the same level solutions as `run` up to rounding, which the tests check.
 
 Notation follows the paper except that n = N - 1 is the number of interior unknowns,
@@ -270,14 +270,14 @@ def level_equation_rows(prob, j: int, rows, levels: List[np.ndarray], u_next: np
 
 
 # ----------------------------------------------------------------------------------------------
-# Constant coefficients (Section 3.2): the Gohberg-Semencul formula after Eq. (3.4), Algorithm
-# "Compute z = A^{-1} v" and Algorithm "Practical implementation of IDS with constant
-# coefficients".  Dense matrices throughout; no FFT.
+# Constant coefficients: the Gohberg-Semencul formula Eq. (3.6) and Algorithm "Compute
+# z = A^{-1} v" (Section 3.1), and Algorithm "Practical implementation of IDS with constant
+# coefficients" (Section 3.2).  Dense matrices throughout; no FFT.
 # ----------------------------------------------------------------------------------------------
 
 
 def gs_generators(A: np.ndarray):
-    """x = A^{-1} e_1 and y = A^{-1} e_n, the two systems of Eq. (3.4), by Gaussian elimination."""
+    """x = A^{-1} e_1 and y = A^{-1} e_n, the two systems of Eq. (3.5), by Gaussian elimination."""
     n = A.shape[0]
     E = np.zeros((n, 2))
     E[0, 0] = 1.0
@@ -333,7 +333,7 @@ def gs_apply(x: np.ndarray, y: np.ndarray, v: np.ndarray) -> np.ndarray:
 def run_const(prob, levels: Optional[int] = None, source: Optional[Callable] = None) -> List[np.ndarray]:
     """Algorithm "Practical implementation of IDS with constant coefficients": level 0 solves
     A^{(sigma)} u^1 = g^1 by elimination; every later level, whose matrix A is the same for
-    j = 1..M-1 when gamma and d_+- are constant (Eq. (3.4) context), computes u^{j+1} = A^{-1} g
+    j = 1..M-1 when gamma and d_+- are constant (Eq. (3.4)), computes u^{j+1} = A^{-1} g
     by Algorithm "Compute z = A^{-1} v" with the generators of that A."""
     gen = {}
 

@@ -681,7 +681,7 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
 }
 
 // ------------------------------------------------------------------------------------------------
-// Constant coefficients: the Gohberg-Semencul formula (Section 3.2, after Eq. (3.4))
+// Constant coefficients: the Gohberg-Semencul formula (Section 3.1, Eq. (3.6))
 //   A^{-1} = (L_p R_p - L0_p R0_p) / xi_0,  x = A^{-1} e_1 = (xi_k), y = A^{-1} e_n = (eta_k),
 //   L_p  lower triangular Toeplitz, first column x;   R_p  upper, first row (eta_{n-1}, ..., eta_0);
 //   L0_p strictly lower, first column (0, eta_0, ..., eta_{n-2});
@@ -805,7 +805,7 @@ __device__ bool residual_pass(const Args &A, const Smem &S, int &rb, RHS b, doub
 }
 
 // Generators of the constant level matrix A (level symbols of j >= 1 in S_A, S_P): the systems
-// A x = e_1 and A y = e_n of Eq. (3.4) by the preconditioned CGS, the factor spectra, one
+// A x = e_1 and A y = e_n of Eq. (3.5) by the preconditioned CGS, the factor spectra, one
 // refinement of each generator with the inverse they define (x += A^{-1}(e_1 - A x)), and the
 // spectra again.  Returns the status; `its` counts the CGS iterations.
 static __device__ int gsf_build(const Args &A, const Smem &S, const Krylov<double2> &V64, int &rb, int &its,

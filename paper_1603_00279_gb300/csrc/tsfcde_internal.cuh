@@ -102,7 +102,7 @@ struct Args {
   ffc *twLff;             // float-float twiddles, L
   // constant coefficients: A^{(j+sigma)} = A for j >= 1, solved by the Gohberg-Semencul formula
   int gsf;                // 1: levels j >= 1 compute u^{j+1} = A^{-1} g (no Krylov iterations)
-  double *gx, *gy;        // generators x = A^{-1} e_1, y = A^{-1} e_n (Eq. (3.4)); L each, zero tail
+  double *gx, *gy;        // generators x = A^{-1} e_1, y = A^{-1} e_n (Eq. (3.5)); L each, zero tail
   double2 *SL, *SR, *SL0, *SR0;   // spectra of L_p / xi_0, R_p, L0_p / xi_0, R0_p (permuted, N+1)
   double2 *Y3;            // third FFT work buffer, N complex
 };

@@ -1,7 +1,7 @@
 """Constant-coefficient path (TSFCDE_ALG_IDS_CONST) against the oracle.
 
 Algorithm "Practical implementation of IDS with constant coefficients" (Section 3.2): level 0 by
-the preconditioned CGS; levels j >= 1 by the Gohberg-Semencul formula (after Eq. (3.4)) applied
+the preconditioned CGS; levels j >= 1 by the Gohberg-Semencul formula (Eq. (3.6)) applied
 as in Algorithm "Compute z = A^{-1} v".  The level solutions are the same as the plain scheme's,
 so the oracle is the plain elimination march (oracle.run); FP64 tolerance 1e-10 per level, as for
 the CGS path.  The generators x = A^{-1} e_1, y = A^{-1} e_n are checked through op 3

@@ -1,6 +1,6 @@
-"""Pins of the oracle's constant-coefficient path (Section 3.2): the Gohberg-Semencul formula after
-Eq. (3.4), Algorithm "Compute z = A^{-1} v" and Algorithm "Practical implementation of IDS with
-constant coefficients".
+"""Pins of the oracle's constant-coefficient path: the generator systems Eq. (3.5), the
+Gohberg-Semencul formula Eq. (3.6) and Algorithm "Compute z = A^{-1} v" (Section 3.1), and
+Algorithm "Practical implementation of IDS with constant coefficients" (Section 3.2).
 
 What fixes them, other than the oracle itself:
   * exact rational arithmetic on tiny Toeplitz matrices: the formula must give the inverse
