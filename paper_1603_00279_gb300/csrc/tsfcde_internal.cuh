@@ -3,8 +3,9 @@
 // Data layout in device memory (one context = one TSFCDE instance):
 //   * real vectors of the level solve (u, x, r, r~, p, q, u_cgs, v^, H) hold n values followed by
 //     zeros up to L = max(8, 2^ceil(log2 2n)), the length of the circulant embedding of an n x n
-//     Toeplitz matrix (Section 3.2: "B u^j can be evaluated by FFTs"); viewed as L/2 complex
-//     numbers z_m = (v_{2m}, v_{2m+1}) they feed a half-length complex FFT (real-input trick);
+//     Toeplitz matrix, through which Section 3.2 evaluates the products with A and B by FFT;
+//     viewed as L/2 complex numbers z_m = (v_{2m}, v_{2m+1}) they feed a half-length complex
+//     FFT (real-input trick);
 //   * FFTs of length N = L/2 are split N = N1 x N2 (four-step): "column" items are the N2
 //     strided lines of N1 points, "row" items are the N1 contiguous lines of N2 points.  Spectra
 //     of Toeplitz kernels are stored in the permuted order slot(k) = (k mod N1) N2 + k / N1
