@@ -133,3 +133,26 @@ def test_binding_fails_loudly_without_the_library():
     import paper_1603_00279_gb300 as P
     with pytest.raises(RuntimeError):
         P.load_library(os.path.join(ROOT, "paper_1603_00279_gb300", "_lib", "missing.so"))
+
+
+def test_empty_and_oversize_problems_rejected_without_device():
+    """N = 0, M = 0 and N beyond 2^22 - 1 are argument errors, as is an empty or oversize batch."""
+    import paper_1603_00279_gb300 as P
+    lib = P.load_library()
+    opt = P.Options()
+    lib.tsfcde_default_options(C.byref(opt))
+    coef = P.COEF_FN(lambda t, u: 1.0)
+    phi = P.FIELD_FN(lambda t, x, out, n, u: None)
+    for N, M in [(0, 4), (15, 0), (1 << 22, 4), (-3, 4)]:
+        ctx = C.c_void_p()
+        st = lib.tsfcde_setup(C.byref(ctx), 0.0, 1.0, 1.0, N, M, 0.5, 1.5, coef, coef, coef, phi,
+                              P.FIELD_FN(), None, C.byref(opt))
+        assert st == 1 and not ctx.value, (N, M)
+    u0 = (C.c_double * 20000)()
+    p0 = C.cast(u0, C.POINTER(C.c_double))
+    h = C.c_void_p()
+    assert lib.tsfcde_batch_setup(C.byref(h), 0, None, 4, C.byref(opt)) == 1
+    big = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 16384, 0.5, 1.5, 0.1, 1.0, 1.0, p0))
+    assert lib.tsfcde_batch_setup(C.byref(h), 1, big, 4, C.byref(opt)) == 1
+    ok = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0, p0))
+    assert lib.tsfcde_batch_setup(C.byref(h), 1, ok, 0, C.byref(opt)) == 1

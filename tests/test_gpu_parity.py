@@ -175,3 +175,34 @@ def test_autotuned_plan_matches_oracle(n):
         s.step(1)
         assert rel_l2(s.get_level()[0], ref[j + 1]) <= 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("case", [
+    dict(alpha=1.0, beta=2.0),                                  # Crank-Nicolson limit (remark after Eq. (2.1))
+    dict(alpha=1.0, beta=1.5),                                  # sigma = 1/2, no history
+    dict(alpha=0.6, beta=2.0),                                  # beta = 2: W tridiagonal
+    dict(alpha=0.05, beta=1.05),                                # near the lower limits of both orders
+    dict(alpha=0.6, beta=1.7, gamma=lambda t: 0.0),             # no convection
+    dict(alpha=0.6, beta=1.7, d_minus=lambda t: 0.0),           # one-sided diffusion
+    dict(alpha=0.6, beta=1.7, d_plus=lambda t: 0.0, gamma=lambda t: -2.0),
+])
+@pytest.mark.parametrize("precond", ["strang", "tchan"])
+def test_degenerate_and_edge_parameters(case, precond):
+    """The march at the edges of Eq. (1.1)'s parameter ranges, every level against elimination."""
+    P = solver_module()
+    prob = W.manufactured(255, 10, preconditioner=precond, **case)
+    ref = O.run(prob)
+    got, it, rs = _march_all_levels(P, prob)
+    assert max(rel_l2(got[j], ref[j]) for j in range(prob.M + 1)) <= 1e-10
+
+
+def test_degenerate_constant_coefficient_parameters():
+    """alpha = 1 and beta = 2 through the constant-coefficient algorithm as well."""
+    P = solver_module()
+    prob = W.manufactured(511, 8, 1.0, 2.0, gamma=lambda t: 0.3, d_plus=lambda t: 0.7,
+                          d_minus=lambda t: 0.4, constant=True)
+    ref = O.run(prob)
+    s = P.Solver.from_problem(prob, algorithm="ids-const")
+    u = s.solve()
+    s.close()
+    assert rel_l2(u, ref[-1]) <= 1e-10

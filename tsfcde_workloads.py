@@ -146,6 +146,14 @@ def _make(n, M, alpha, beta, gamma, dp, dm, manuf, **kw):
 # Workloads
 # --------------------------------------------------------------------------------------------
 
+def manufactured(n, M, alpha, beta, gamma=lambda t: 0.5, d_plus=lambda t: 1.0 + t,
+                 d_minus=lambda t: 1.0 - 0.5 * t, preconditioner="strang", constant=False):
+    """Any parameters with the manufactured solution u = (t^2+1) x^2 (1-x)^2 on [0, 1] and its
+    analytic source (edge and degenerate cases of Eq. (1.1))."""
+    return _make(n, M, alpha, beta, gamma, d_plus, d_minus, manufactured_t2,
+                 preconditioner=preconditioner, constant_coefficients=constant, name="manufactured")
+
+
 def config_small(n=127, M=64, alpha=0.6, beta=1.7, preconditioner="strang"):
     """Small FP64 instance: n=127, M=64, alpha=0.6, beta=1.7, gamma=0.5, d+=1+t, d-=1-t/2."""
     return _make(n, M, alpha, beta, lambda t: 0.5, lambda t: 1.0 + t, lambda t: 1.0 - 0.5 * t,
