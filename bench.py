@@ -113,8 +113,9 @@ def workload(name: str, precond):
         p = W.config_large()
     elif name == "small":
         p = W.config_small()
-    elif name == "mixed":
+    elif name in ("mixed", "precision"):
         p = W.config_mixed()
+        p.name = name
     elif name == "batch":
         return W.config_batch(count=_ARGS.instances or 4096)
     elif name == "history":
@@ -128,6 +129,8 @@ def workload(name: str, precond):
 
 def describe(p) -> dict:
     name = "history" if p.name.startswith("history") else p.name
+    if name == "mixed":
+        name = "precision"
     return {"workload": f"tsfcde_{name}", "n": p.n, "M": p.M, "alpha": p.alpha, "beta": p.beta,
             "preconditioner": p.preconditioner, "tol": p.tol, "source": "separable(4)",
             "updates_per_step": p.n * p.M}
@@ -234,7 +237,8 @@ def oracle_sample(p, budget_s: float = 15.0):
     if p.name.startswith("history"):
         q = W.config_history(n=n_s, M=p.M)[int(p.name[len("history"):])]
     else:
-        cls = {"large": W.config_large, "small": W.config_small, "mixed": W.config_mixed}[p.name]
+        cls = {"large": W.config_large, "small": W.config_small, "mixed": W.config_mixed,
+               "precision": W.config_mixed}[p.name]
         q = cls(n=n_s, M=p.M)
     q.preconditioner = p.preconditioner
     t0 = time.perf_counter()
@@ -249,9 +253,9 @@ def oracle_sample(p, budget_s: float = 15.0):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     desc = (f"oracle (dense LU per level, numpy/LAPACK) on the workload's alpha, beta and "
             f"coefficients at n={n_s} (workload n={p.n}), levels 0..{levels - 1} of M={p.M}; "
-            f"{dt:.1f} s; dense LU costs grow as n^3 per level, so at the workload's n the "
-            f"oracle is ~{(p.n / n_s) ** 2:.0f}x slower per update than this sample")
-    return n_s * levels / dt, desc, cores, dt
+            f"{dt:.1f} s; value scaled to the workload's n by the n^-2 law of dense LU "
+            f"(x{(n_s / p.n) ** 2:.3g})")
+    return n_s * levels / dt, desc, cores, dt, n_s, levels
 
 
 def oracle_single_core(p):
@@ -267,7 +271,8 @@ def oracle_single_core(p):
         "if name.startswith('history'):\n"
         "    q = W.config_history(n=n_s, M=M)[int(name[7:])]\n"
         "else:\n"
-        "    q = {'large': W.config_large, 'small': W.config_small, 'mixed': W.config_mixed}[name](n=n_s, M=M)\n"
+        "    q = {'large': W.config_large, 'small': W.config_small, 'mixed': W.config_mixed,\n"
+        "         'precision': W.config_mixed}[name](n=n_s, M=M)\n"
         "t0 = time.perf_counter(); O.run(q, levels=1); dt = time.perf_counter() - t0\n"
         "print(json.dumps(n_s / dt))\n")
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -281,26 +286,32 @@ def oracle_single_core(p):
 
 
 def run_reference(args, p):
+    """The reference arm: the FP64 CPU oracle timed on the host cores, each step a bounded sample
+    of the workload (its parameters at n = 2047), reported at the workload's n by the dense-LU
+    law like cpu_baseline; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     vals, descs = [], []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
+    for _ in range(min(args.warmup, 1)):
         oracle_sample(p, budget_s=2.0)
     t_all = 0.0
+    n_s = levels = 0
     for _ in range(args.steps):
-        v, d, cores, dt = oracle_sample(p, budget_s=20.0)
+        v, d, cores, dt, n_s, levels = oracle_sample(p, budget_s=args.ref_budget)
         vals.append(v)
         t_all += dt
         descs.append(d)
-    v = float(np.mean(vals))
+    v_sample = float(np.mean(vals))
+    v = v_sample * (n_s / p.n) ** 2
     line = {"metric": "grid-point updates/s", "value": v, "unit": "updates/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution)",
-            "config": describe(p),
+            "config": {**describe(p), "oracle_sample_n": n_s},
             "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
-                             "sample": descs[-1]},
+                             "sample": descs[-1], "extrapolated": p.n != n_s,
+                             "measured_sample": {"n": n_s, "levels": levels, "value": v_sample}},
             "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -344,6 +355,63 @@ def run_reference_batch(args, probs):
 # ---------------------------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------------------------
+def kernel_sources_sha() -> str:
+    """sha256 over the CUDA sources (sorted by name): identifies the kernels an ncu capture saw."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1603_00279_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(name: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel
+    from the committed ncu summary profiles/<name>, if that capture saw the current kernel sources
+    (its `kernel_sources_sha256` line); else (None, reason)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None, f"no capture ({name})"
+    kv = {}
+    for l in lines:
+        if ":" in l and l.strip().startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
+            k, v = l.split(":", 1)
+            kv[k.strip().lstrip("-* `")] = v.strip().strip("`")
+    try:
+        traffic = float(kv["traffic_bytes_per_launch"])
+        sha = kv["kernel_sources_sha256"]
+    except (KeyError, ValueError):
+        return None, f"capture {name} has no traffic line"
+    if sha != kernel_sources_sha():
+        return None, f"kernel sources changed since the capture in profiles/{name}"
+    return traffic, f"ncu capture, profiles/{name}"
+
+
+def estimate_total_s(march_s: float, setup_s: float, steps: int, warmup: int, cpu_budget: float,
+                     mixed_march_s: float = 0.0) -> float:
+    """Wall time of one default single-instance bench run: warm-up and timed marches, the e2e
+    march, the mixed-precision leg (one march plus its setup), the CPU oracle leg (the timed
+    sample plus one single-core level) and setup."""
+    marches = warmup + steps + 1
+    return setup_s * 2 + marches * march_s + 1.2 * mixed_march_s + 1.5 * cpu_budget + 30.0
+
+
+def level_gap(s_ref, s_other, levels):
+    """Relative L2 gap per level between two marches (levels rebuilt through tsfcde_get_level)."""
+    out = {}
+    for j in levels:
+        a, _ = s_ref.get_level(j)
+        b, _ = s_other.get_level(j)
+        den = float(np.linalg.norm(a))
+        out[int(j)] = float(np.linalg.norm(b - a) / (den if den > 0 else 1.0))
+    return out
+
+
 def run_native(args, p):
     import torch
     import torch.distributed as dist
@@ -361,10 +429,11 @@ def run_native(args, p):
     import paper_1603_00279_gb300 as P
 
     stream = torch.cuda.Stream()
+    lpl = args.levels_per_launch
     t_setup = time.perf_counter()
     s = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
                               maxit=args.maxit, precision=args.precision,
-                              autotune=not args.no_autotune)
+                              autotune=not args.no_autotune, levels_per_launch=lpl)
     setup_ms = 1e3 * (time.perf_counter() - t_setup)
     plan = s.plan()
     n, M = p.n, p.M
@@ -375,8 +444,7 @@ def run_native(args, p):
 
     for _ in range(args.warmup):
         one_step()
-    it, _ = s.history(M)
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, one whole march per step
     stats = []
     if world > 1:
         dist.barrier()
@@ -399,7 +467,8 @@ def run_native(args, p):
     value = world * n * M * args.steps / (ms_max / 1e3)
     it, res = s.history(M)
     launches = int(sum(st["device_launches"] for st in stats))
-    kernel_ms = float(np.mean([st["device_ms"] for st in stats]))
+    launches_per_step = launches / max(1, len(stats))
+    kernel_ms = float(np.mean([st["device_ms"] for st in stats]))   # per march, all its launches
     newsym = M if p.name != "batch" else 2
     flops = algorithmic_flops(p, it, newsym)
     if args.precision == "mixed":   # one FP64 residual product per refinement step
@@ -430,17 +499,17 @@ def run_native(args, p):
                 "ms": hms, "fp64_tflops": 2.0 * n * jh / (hms / 1e3) / 1e12,
                 "peak_source": peak[1]}
 
-    # end to end through the C ABI with pinned host buffers: H2D of u^0, D2H of u^M per step
-    u0 = torch.from_numpy(np.ascontiguousarray(p.phi(p.grid()))).pin_memory()
+    # end to end through the C ABI with pinned host buffers: H2D of u^0, the march, D2H of u^M;
+    # u^0 is the library's own sample of phi on its mesh (level 0 read back after a reset)
+    s.reset()
+    u0 = torch.from_numpy(s.get_level(0)[0]).pin_memory()
     uM = torch.empty(n, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, args.steps // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.reset(u0_ptr=u0.data_ptr())
-        s.solve(out_ptr=uM.data_ptr())
+    s.reset(u0_ptr=u0.data_ptr())
+    s.solve(out_ptr=uM.data_ptr())
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = time.perf_counter() - t0
     tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -449,6 +518,42 @@ def run_native(args, p):
     # accuracy of the march against the manufactured solution (a property at any size)
     u_end = uM.numpy()
     err = float(np.sqrt(p.h) * np.linalg.norm(u_end - p.exact(p.grid(), p.T)))
+
+    # mixed-precision leg of the precision workload: one timed march, and its per-level gap to
+    # the FP64 march above (both contexts hold every level through their increment rings)
+    mixed = None
+    if args.precision == "fp64" and args.mixed_leg and world == 1:
+        ts = time.perf_counter()
+        sm = P.Solver.from_problem(p, source="separable", device=local, stream=stream.cuda_stream,
+                                   maxit=args.maxit, precision="mixed",
+                                   autotune=not args.no_autotune, levels_per_launch=lpl)
+        msetup = 1e3 * (time.perf_counter() - ts)
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        mst = sm.step(M)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        levels = sorted(set(list(range(1, min(M, 8) + 1)) +
+                        [j for j in (16, 32, 64, 128, 256, M // 2, 3 * M // 4, M - 1, M) if 1 <= j <= M]))
+        gaps = level_gap(s, sm, levels)
+        um = sm.get_level(M)[0]
+        merr = float(np.sqrt(p.h) * np.linalg.norm(um - p.exact(p.grid(), p.T)))
+        mixed = {"value": n * M / (mms / 1e3), "unit": "updates/s", "ms_per_march": mms,
+                 "vs_fp64": (n * M / (mms / 1e3)) / value,
+                 "rel_l2_gap_to_fp64_by_level": gaps,
+                 "max_gap_levels_1_8": max(gaps[j] for j in levels if j <= 8),
+                 "max_gap": max(gaps.values()),
+                 "l2_error_vs_exact_at_T": merr,
+                 "refinement_steps": int(mst["outer_iterations"]),
+                 "escalated_levels": int(mst["escalated_levels"]),
+                 "floor_levels": int(mst["floor_levels"]),
+                 "cgs_iterations": int(mst["total_iterations"]),
+                 "setup_ms": msetup,
+                 "dtype": "f32 / float-float inner, f64 refinement, history and weights"}
+        sm.close()
     s.close()
 
     if rank != 0:
@@ -456,6 +561,11 @@ def run_native(args, p):
             dist.destroy_process_group()
         return
     clocks = clk.summary()
+    traffic, tsrc = captured_traffic(args.traffic_profile) if lpl == 64 else (None, "launch shape differs from the capture")
+    rl = roofline("level_kernel", flops / launches_per_step, kernel_ms / launches_per_step, args.precision)
+    rl["traffic"] = traffic
+    rl["traffic_source"] = tsrc
+    rl["per"] = f"launch ({lpl or M} levels; {launches_per_step:.0f} launches per march)"
     line = {
         "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -463,12 +573,14 @@ def run_native(args, p):
         "dtype": "f64" if args.precision == "fp64" else "f32 inner / f64 refinement",
         "data": "synthetic (manufactured solution u=(t^2+1)x^2(1-x)^2, analytic source)",
         "config": {**describe(p), "parallelism": f"replicas{world}", "fft_plan": plan,
-                   "l2": "inputs larger than L2 (history ring %.0f MB)" % (M * n * 8 / 1e6)},
+                   "levels_per_launch": lpl,
+                   "l2": "inputs larger than L2 (history ring %.0f MB, work arrays %.0f MB)"
+                         % (M * n * 8 / 1e6, 24 * n * 8 / 1e6)},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n},
+                "d2h_bytes_per_step": 8 * n, "marches": 1},
         "gpu_launches": launches,
         "setup_ms": setup_ms,
-        "roofline": roofline("level_kernel", flops, kernel_ms, args.precision),
+        "roofline": rl,
         "history_roofline": hist,
         "cgs_iterations": {"mean": float(it.mean()), "min": int(it.min()), "max": int(it.max()),
                            "levels_at_maxit": int((it >= args.maxit).sum())},
@@ -477,15 +589,27 @@ def run_native(args, p):
                         "escalated_levels": int(sum(st["escalated_levels"] for st in stats)) // max(1, args.steps)}
                        if args.precision == "mixed" else None),
         "l2_error_vs_exact_at_T": err,
+        "mixed": mixed,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
-        v, d, cores, _ = oracle_sample(p, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
-                                "sample": d, "single_core": oracle_single_core(p)}
+        line["cpu_baseline"] = cpu_baseline_line(p, args.cpu_budget)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def cpu_baseline_line(p, budget_s):
+    """The oracle timed on a bounded sample (the workload's parameters at n = 2047), reported at
+    the workload's n by the dense-LU law: elimination costs 2/3 n^3 flops per level, so updates/s
+    scale as n^-2.  The measured sample is kept beside it."""
+    v, d, cores, dt, n_s, levels = oracle_sample(p, budget_s=budget_s)
+    scale = (n_s / p.n) ** 2
+    return {"value": v * scale, "unit": "updates/s", "cores": cores, "kind": "oracle",
+            "sample": d, "extrapolated": p.n != n_s,
+            "law": "dense LU per level: 2/3 n^3 flop, so updates/s ~ n^-2",
+            "measured_sample": {"n": n_s, "levels": levels, "seconds": dt, "value": v},
+            "single_core": oracle_single_core(p)}
 
 
 def run_native_batch(args, probs_all):
@@ -546,17 +670,15 @@ def run_native_batch(args, probs_all):
             flops += _alg_flops(p.n, M, precond, it, 2)
     its_all = np.concatenate(its_all)
     # end to end: H2D of every u^0, march, D2H of every u^M through the C ABI
-    u0 = torch.from_numpy(np.concatenate([np.asarray(p.phi(p.grid()), dtype=np.float64)
-                                          for p in probs])).pin_memory()
+    b.reset()
+    u0 = torch.from_numpy(np.concatenate([b.get_level(i, 0)[0] for i in range(len(probs))])).pin_memory()
     uM = torch.empty(ntot, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, args.steps // 2)
-    for _ in range(e2e_steps):
-        b.set_initial(u0.data_ptr())
-        b.step(M)
-        b.get_all(uM.data_ptr())
-    e2e_s = ranks.max((time.perf_counter() - t0) / e2e_steps)
+    b.set_initial(u0.data_ptr())
+    b.step(M)
+    b.get_all(uM.data_ptr())
+    e2e_s = ranks.max(time.perf_counter() - t0)
     b.close()
     if ranks.rank != 0:
         return
@@ -693,7 +815,7 @@ def run_native_history(args, probs):
     launches = int(sum(st["device_launches"] for step in stats for st in step))
     # end to end through the C ABI: H2D of u^0 and D2H of u^M per instance from pinned memory
     import torch as _t
-    u0s = [_t.from_numpy(np.ascontiguousarray(q.phi(q.grid()))).pin_memory() for q in probs]
+    u0s = [_t.from_numpy(s.get_level(0)[0]).pin_memory() for s in ctxs]
     uMs = [_t.empty(q.n, dtype=_t.float64).pin_memory() for q in probs]
     _t.cuda.synchronize()
     t0 = time.perf_counter()
@@ -730,9 +852,7 @@ def run_native_history(args, probs):
             "cgs_iterations_mean": float(np.mean(its)), "l2_error_vs_exact_at_T": errs,
             "convergence_order": co, "clocks": clk.summary()}
     if not args.no_cpu_baseline:
-        v, d, cores, _ = oracle_sample(probs[0], budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
-                                "sample": d}
+        line["cpu_baseline"] = cpu_baseline_line(probs[0], args.cpu_budget)
     print(json.dumps(line))
 
 
@@ -742,7 +862,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="large")
+    ap.add_argument("--workload", default="precision",
+                    help="precision (default: n = 2^20-1, M = 512, FP64 with a mixed leg), large, "
+                         "small, mixed (precision workload in mixed precision), batch, history")
     ap.add_argument("--precond", default=None, choices=[None, "strang", "tchan", "none"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"],
                     help="default: fp64, or mixed for the mixed and history workloads")
@@ -750,6 +872,14 @@ def main():
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0,
+                    help="--impl reference: seconds of oracle work per step")
+    ap.add_argument("--levels-per-launch", type=int, default=64,
+                    help="levels per device launch of the single-instance march (0: one launch)")
+    ap.add_argument("--traffic-profile", default="level_kernel_precision_n1048575_dram.md",
+                    help="profiles/ summary holding the dominant kernel's DRAM bytes per launch")
+    ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
+                    help="precision workload: skip the mixed-precision march and its gap")
     ap.add_argument("--instances", type=int, default=None,
                     help="batch workload: instance count (4096); history workload: how many of "
                          "its 16 instances to march (1)")

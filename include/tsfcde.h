@@ -49,6 +49,14 @@ extern "C" {
 #define TSFCDE_E_STATE 9            /* stepping past level M, or a call in the wrong state        */
 #define TSFCDE_E_NO_DEVICE 10       /* no CUDA device / library built without a usable GPU        */
 
+/* ---- callbacks (host functions, called only during setup, on the caller's thread) ----------- */
+/* gamma(t), d_plus(t), d_minus(t) of Eq. (1.1); called at t_{j+sigma} = (j+sigma) tau. */
+typedef double (*tsfcde_coef_fn)(double t, void *user);
+/* Vectorized field: out[i] = F(x[i], t) for i < n.  The library passes its own mesh x_i = a + i h
+ * (i = 1..N, Section 2.1).  phi is called once with t = 0; f is called once per level with
+ * t = t_{j+sigma} (Eq. (2.1) evaluates f at t_{j+sigma}). */
+typedef void (*tsfcde_field_fn)(double t, const double *x, double *out, int64_t n, void *user);
+
 /* ---- options -------------------------------------------------------------------------------- */
 #define TSFCDE_PRECOND_STRANG 0 /* Strang circulant s(.) of Eq. (3.7) (the paper's choice)       */
 #define TSFCDE_PRECOND_TCHAN 1  /* T. Chan's optimal circulant in place of s(.)                  */
@@ -69,13 +77,14 @@ typedef struct tsfcde_options {
                              A level that reaches it keeps its minimum-residual iterate.    */
   int32_t device;         /* CUDA device ordinal; default 0                                 */
   /* Separable source f(x,t) = sum_r T_r(t) X_r(x) (used when source_rank > 0, in which case the
-   * f callback of tsfcde_setup must be NULL):
-   *   source_x: source_rank rows of N values, X_r(x_i), row-major, host;
-   *   source_t: source_rank rows of M values, T_r(t_{j+sigma}) for j = 0..M-1, row-major, host.
-   * Both are copied during setup. */
+   * f callback of tsfcde_setup must be NULL).  Both arrays hold source_rank host callbacks and
+   * are read during setup only: the library calls source_space[r] once on its mesh x_i
+   * (t argument 0) and source_time[r] once per level at t_{j+sigma}, with tsfcde_setup's `user`;
+   * the device rebuilds f^{j+sigma}_i = sum_r T_r(t_{j+sigma}) X_r(x_i) at every level from these
+   * R (N + M) values instead of an M x N table. */
   int32_t source_rank;
-  const double *source_x;
-  const double *source_t;
+  const tsfcde_field_fn *source_space;
+  const tsfcde_coef_fn *source_time;
   int32_t levels_per_launch; /* device launches cover at most this many levels; 0 = no limit */
   void *stream;              /* cudaStream_t to run on (e.g. a PyTorch stream); NULL = the
                                 library creates and owns a non-blocking stream               */
@@ -97,7 +106,24 @@ typedef struct tsfcde_options {
                                 product and keep the fastest (see tsfcde_get_plan); 0: default
                                 plan (N1 <= N2, N1 >= N2/2, chunks of 4096 values)            */
   int32_t algorithm;         /* TSFCDE_ALG_IDS (default) or TSFCDE_ALG_IDS_CONST, below        */
+  int32_t test_inject;       /* testing hook, 0 normally (TSFCDE_INJECT_*, below): makes one
+                                failure path reachable from the host with valid inputs        */
 } tsfcde_options;
+
+/* Testing hooks (tsfcde_options.test_inject).  Valid problems cannot reach these failure paths
+ * (Theorems 1 and 4 keep A and P nonsingular, and a level's first CGS denominator is positive),
+ * so a host-set hook stands in for the condition; nothing faults on the GPU.
+ *   NOMEM:     tsfcde_setup / tsfcde_batch_setup report their device allocation as failed
+ *              (no allocation is attempted) and return TSFCDE_E_NOMEM after releasing
+ *              everything;
+ *   BREAKDOWN: the first CGS iteration of the first level advanced by a context sees
+ *              (r~, A p^) = 0 and the step returns TSFCDE_E_BREAKDOWN;
+ *   SINGULAR:  the first level's preconditioner check sees a vanishing eigenvalue of P and the
+ *              step returns TSFCDE_E_SINGULAR_PRECOND. */
+#define TSFCDE_INJECT_NONE 0
+#define TSFCDE_INJECT_NOMEM 1
+#define TSFCDE_INJECT_BREAKDOWN 2
+#define TSFCDE_INJECT_SINGULAR 3
 
 /* Level algorithm.
  * TSFCDE_ALG_IDS: Algorithm "Practical implementation of IDS" -- every level solved by the
@@ -152,13 +178,6 @@ typedef struct tsfcde_stats {
   int32_t pad_;
 } tsfcde_stats;
 
-/* ---- callbacks (host functions, called only inside tsfcde_setup on the caller's thread) ------ */
-/* gamma(t), d_plus(t), d_minus(t) of Eq. (1.1); called at t_{j+sigma} = (j+sigma) tau. */
-typedef double (*tsfcde_coef_fn)(double t, void *user);
-/* Vectorized field: out[i] = F(x[i], t) for i < n.  phi is called once with t = 0; f is called
- * once per level with t = t_{j+sigma} (Eq. (2.1) evaluates f at t_{j+sigma}). */
-typedef void (*tsfcde_field_fn)(double t, const double *x, double *out, int64_t n, void *user);
-
 typedef struct tsfcde_ctx tsfcde_ctx;
 
 /* ---- life cycle ----------------------------------------------------------------------------- */
@@ -189,8 +208,27 @@ int tsfcde_step(tsfcde_ctx *ctx, int64_t nsteps, tsfcde_stats *stats);
 /* Advance to level M and copy u^M (N values) to the host buffer u_out (may be NULL). */
 int tsfcde_solve(tsfcde_ctx *ctx, double *u_out, tsfcde_stats *stats);
 
-/* Copy the current level u^j to the host buffer u_out (N values); *level receives j. */
-int tsfcde_get_level(tsfcde_ctx *ctx, double *u_out, int64_t *level);
+/* Copy level u^j of the current march to the host buffer u_out (N values), for any
+ * 0 <= j <= current level (E_INVALID_ARG otherwise).  Algorithm "Practical implementation of IDS"
+ * produces every level; the context keeps u^0 of the march, the current level u^c and the ring of
+ * increments d^s = u^{s+1} - u^s (s < c) that the history sum of Lemma 1 reads, so u^j is rebuilt
+ * on the device by the shorter of the two sums u^0 + sum_{s<j} d^s and u^c - sum_{j<=s<c} d^s,
+ * in FP64 in a fixed order.  j = 0 and j = c return the stored vectors exactly; in between the
+ * rebuilt level differs from the march's own u^j by at most (number of terms) * u64 * sum |d^s|
+ * per element.  Does not change the march state. */
+int tsfcde_get_level(tsfcde_ctx *ctx, int64_t j, double *u_out);
+
+/* The current level c of the march (the context holds u^c). */
+int tsfcde_level(tsfcde_ctx *ctx, int64_t *level);
+
+/* The spatial weights the context computed at setup, for k = 0..N+1 (N+2 host values each; either
+ * pointer may be NULL): g_out[k] = g_k, the Grunwald weights (-1)^k binom(beta, k) by the
+ * recurrence g_k = (1 - (beta+1)/k) g_{k-1} of Lemma 3, and omega_out[k] = omega_k, the WSGD
+ * weights of Lemma 2 (omega_0 = lambda_1 g_0, omega_1 = lambda_1 g_1 + lambda_0 g_0,
+ * omega_k = lambda_1 g_k + lambda_0 g_{k-1} + lambda_{-1} g_{k-2}).  Every operation is a single
+ * IEEE-754 binary64 operation, rounded to nearest, evaluated left to right (no contraction into
+ * fused multiply-adds), so the values are reproducible bit for bit on any conforming host. */
+int tsfcde_get_weights(tsfcde_ctx *ctx, double *g_out, double *omega_out);
 
 /* Return to level 0.  u0: N host values to use as u^0 (copied host to device), or NULL for
  * phi(x_i) (restored from a device copy made at setup; no host transfer). */
@@ -241,7 +279,9 @@ typedef struct tsfcde_instance {
   int64_t N;              /* interior points, 1 <= N <= 16383                               */
   double alpha, beta;     /* orders, as in tsfcde_setup                                      */
   double gamma, d_plus, d_minus;   /* constant coefficients (d_plus, d_minus >= 0)          */
-  const double *u0;       /* N host values of u^0 (copied during setup)                     */
+  tsfcde_field_fn phi;    /* initial value: called once during tsfcde_batch_setup with t = 0 on
+                             the instance's mesh x_i = a + i h, i = 1..N (u^0_i = phi(x_i))   */
+  void *user;             /* passed through to phi                                          */
 } tsfcde_instance;
 
 typedef struct tsfcde_batch tsfcde_batch;
@@ -252,8 +292,12 @@ int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance 
                        const tsfcde_options *opt);
 /* Advance every instance by nsteps levels (one device launch).  stats sums over instances. */
 int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats);
-/* Copy instance i's current level (N_i host values); *level receives j. */
-int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, double *u_out, int64_t *level);
+/* Copy level u^j of instance i (N_i host values), for any 0 <= j <= the batch's current level,
+ * rebuilt from the instance's u^0, current level and ring of increments exactly as
+ * tsfcde_get_level does. */
+int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, int64_t j, double *u_out);
+/* The batch's current level (every instance is at the same level). */
+int tsfcde_batch_level(tsfcde_batch *b, int64_t *level);
 /* Per-level CGS iterations and final residuals of instance i, levels 0..count-1. */
 int tsfcde_batch_get_history(tsfcde_batch *b, int64_t i, int32_t *iters, double *resid, int64_t count);
 /* Every instance back to level 0 with its u^0 (device copy, no host transfer). */

@@ -30,6 +30,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 INNER = {"auto": 0, "fp32": 1, "ff": 2}
 OPS = {"A": 0, "B": 1, "Pinv": 2, "Ainv_gs": 3}
 ALGORITHMS = {"ids": 0, "ids-const": 1}
+INJECT = {None: 0, "nomem": 1, "breakdown": 2, "singular": 3}
 
 COEF_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 FIELD_FN = C.CFUNCTYPE(None, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -39,12 +40,12 @@ FIELD_FN = C.CFUNCTYPE(None, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_do
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("preconditioner", C.c_int32), ("tol", C.c_double),
                 ("maxit", C.c_int32), ("device", C.c_int32), ("source_rank", C.c_int32),
-                ("source_x", C.POINTER(C.c_double)), ("source_t", C.POINTER(C.c_double)),
+                ("source_space", C.POINTER(FIELD_FN)), ("source_time", C.POINTER(COEF_FN)),
                 ("levels_per_launch", C.c_int32), ("stream", C.c_void_p),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
                 ("barrier_spin_log2", C.c_int32), ("test_skip_arrival", C.c_int32),
                 ("inner_precision", C.c_int32), ("autotune", C.c_int32),
-                ("algorithm", C.c_int32)]
+                ("algorithm", C.c_int32), ("test_inject", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -63,7 +64,8 @@ class Stats(C.Structure):
 class Instance(C.Structure):
     _fields_ = [("a", C.c_double), ("b", C.c_double), ("T", C.c_double), ("N", C.c_int64),
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("d_plus", C.c_double), ("d_minus", C.c_double), ("u0", C.POINTER(C.c_double))]
+                ("d_plus", C.c_double), ("d_minus", C.c_double), ("phi", FIELD_FN),
+                ("user", C.c_void_p)]
 
 
 class TsfcdeError(RuntimeError):
@@ -95,8 +97,12 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_step.restype = C.c_int
     lib.tsfcde_solve.argtypes = [vp, pd, C.POINTER(Stats)]
     lib.tsfcde_solve.restype = C.c_int
-    lib.tsfcde_get_level.argtypes = [vp, pd, C.POINTER(i64)]
+    lib.tsfcde_get_level.argtypes = [vp, i64, pd]
     lib.tsfcde_get_level.restype = C.c_int
+    lib.tsfcde_level.argtypes = [vp, C.POINTER(i64)]
+    lib.tsfcde_level.restype = C.c_int
+    lib.tsfcde_get_weights.argtypes = [vp, pd, pd]
+    lib.tsfcde_get_weights.restype = C.c_int
     lib.tsfcde_reset.argtypes = [vp, pd]
     lib.tsfcde_reset.restype = C.c_int
     lib.tsfcde_get_history.argtypes = [vp, C.POINTER(i32), pd, i64]
@@ -113,8 +119,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_batch_setup.restype = C.c_int
     lib.tsfcde_batch_step.argtypes = [vp, i64, C.POINTER(Stats)]
     lib.tsfcde_batch_step.restype = C.c_int
-    lib.tsfcde_batch_get_level.argtypes = [vp, i64, pd, C.POINTER(i64)]
+    lib.tsfcde_batch_get_level.argtypes = [vp, i64, i64, pd]
     lib.tsfcde_batch_get_level.restype = C.c_int
+    lib.tsfcde_batch_level.argtypes = [vp, C.POINTER(i64)]
+    lib.tsfcde_batch_level.restype = C.c_int
     lib.tsfcde_batch_get_history.argtypes = [vp, i64, C.POINTER(i32), pd, i64]
     lib.tsfcde_batch_get_history.restype = C.c_int
     lib.tsfcde_batch_reset.argtypes = [vp]
@@ -156,7 +164,8 @@ class Solver:
 
     gamma, d_plus, d_minus: callables t -> float.  phi: callable x (ndarray) -> ndarray.
     f: callable (x ndarray, t) -> ndarray, or None; alternatively `separable` = list of
-    (T_r(t), X_r(x)) pairs, evaluated here on the grid and passed as the separable source.
+    (T_r(t), X_r(x)) pairs passed as callbacks; the library samples them on its own mesh.
+    test_inject: None, or "nomem" / "breakdown" / "singular" (tsfcde_options.test_inject).
     """
 
     def __init__(self, a, b, T, N, M, alpha, beta, gamma: Callable, d_plus: Callable,
@@ -167,12 +176,9 @@ class Solver:
                  inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
                  outer_maxit: Optional[int] = None, barrier_spin_log2: Optional[int] = None,
                  test_skip_arrival: bool = False, inner: str = "auto", autotune: bool = False,
-                 algorithm: str = "ids"):
+                 algorithm: str = "ids", test_inject: Optional[str] = None):
         self.lib = load_library()
         self.N, self.M = int(N), int(M)
-        self.h = (b - a) / (N + 1)
-        self.tau = T / M
-        sigma = 1.0 - alpha / 2.0
         self._keep = []
 
         def coef(fn):
@@ -184,7 +190,7 @@ class Solver:
             def call(t, xp, outp, n, _u):
                 x = np.ctypeslib.as_array(xp, shape=(n,))
                 out = np.ctypeslib.as_array(outp, shape=(n,))
-                out[:] = fn(x, t) if with_t else fn(x)
+                out[:] = np.broadcast_to(fn(x, t) if with_t else fn(x), (n,))
             cb = FIELD_FN(call)
             self._keep.append(cb)
             return cb
@@ -210,19 +216,17 @@ class Solver:
         opt.inner_precision = INNER[inner]
         opt.autotune = 1 if autotune else 0
         opt.algorithm = ALGORITHMS[algorithm]
+        opt.test_inject = INJECT[test_inject]
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
                 raise ValueError("give either f or separable")
-            x = a + self.h * np.arange(1, N + 1, dtype=np.float64)
-            ts = (np.arange(M, dtype=np.float64) + sigma) * self.tau
-            sx = np.ascontiguousarray([np.broadcast_to(Xr(x), x.shape) for _, Xr in separable],
-                                      dtype=np.float64)
-            st = np.ascontiguousarray([[Tr(t) for t in ts] for Tr, _ in separable], dtype=np.float64)
-            self._keep += [sx, st]
+            spaces = (FIELD_FN * len(separable))(*[field(Xr, False) for _, Xr in separable])
+            times = (COEF_FN * len(separable))(*[coef(Tr) for Tr, _ in separable])
+            self._keep += [spaces, times]
             opt.source_rank = len(separable)
-            opt.source_x = _dptr(sx)
-            opt.source_t = _dptr(st)
+            opt.source_space = C.cast(spaces, C.POINTER(FIELD_FN))
+            opt.source_time = C.cast(times, C.POINTER(COEF_FN))
         ctx = C.c_void_p()
         stt = self.lib.tsfcde_setup(C.byref(ctx), a, b, T, self.N, self.M, alpha, beta, coef(gamma),
                                     coef(d_plus), coef(d_minus), field(phi, False), f_cb, None,
@@ -259,11 +263,26 @@ class Solver:
         self.last_stats = s.as_dict()
         return out if out_ptr is None else None
 
-    def get_level(self):
-        out = np.empty(self.N)
+    def level(self) -> int:
+        """The current level j of the march."""
         j = C.c_int64()
-        _check(self.lib.tsfcde_get_level(self.ctx, _dptr(out), C.byref(j)), "tsfcde_get_level")
-        return out, j.value
+        _check(self.lib.tsfcde_level(self.ctx, C.byref(j)), "tsfcde_level")
+        return j.value
+
+    def get_level(self, j: Optional[int] = None):
+        """(u^j, j) for any j <= the current level (default: the current level)."""
+        cur = self.level()
+        j = cur if j is None else int(j)
+        out = np.empty(self.N)
+        _check(self.lib.tsfcde_get_level(self.ctx, j, _dptr(out)), "tsfcde_get_level")
+        return out, j
+
+    def weights(self):
+        """(g_k, omega_k) for k = 0..N+1 as the library computed them (Lemmas 2-3)."""
+        g = np.empty(self.N + 2)
+        w = np.empty(self.N + 2)
+        _check(self.lib.tsfcde_get_weights(self.ctx, _dptr(g), _dptr(w)), "tsfcde_get_weights")
+        return g, w
 
     def reset(self, u0: Optional[np.ndarray] = None, u0_ptr: Optional[int] = None):
         """Back to level 0 with u^0 = u0 (numpy), the host address u0_ptr, or phi."""
@@ -329,18 +348,26 @@ class Batch:
     def __init__(self, problems, M: int, preconditioner: str = "strang", tol: float = 1e-12,
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
                  stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids",
-                 inner_tol: Optional[float] = None, autotune: bool = False):
+                 inner_tol: Optional[float] = None, autotune: bool = False,
+                 test_inject: Optional[str] = None):
         self.lib = load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
-        self._u0 = []
+        self._keep = []
+
+        def field(fn):
+            def call(t, xp, outp, n, _u):
+                x = np.ctypeslib.as_array(xp, shape=(n,))
+                out = np.ctypeslib.as_array(outp, shape=(n,))
+                out[:] = np.broadcast_to(fn(x), (n,))
+            cb = FIELD_FN(call)
+            self._keep.append(cb)
+            return cb
+
         arr = (Instance * len(problems))()
         for k, p in enumerate(problems):
-            x = p.a + (p.b - p.a) / (p.n + 1) * np.arange(1, p.n + 1, dtype=np.float64)
-            u0 = np.ascontiguousarray(p.phi(x), dtype=np.float64)
-            self._u0.append(u0)
             arr[k] = Instance(p.a, p.b, p.T, p.n, p.alpha, p.beta, float(p.gamma(0.0)),
-                              float(p.d_plus(0.0)), float(p.d_minus(0.0)), _dptr(u0))
+                              float(p.d_plus(0.0)), float(p.d_minus(0.0)), field(p.phi), None)
         opt = Options()
         self.lib.tsfcde_default_options(C.byref(opt))
         opt.preconditioner = PRECONDITIONERS[preconditioner]
@@ -354,6 +381,7 @@ class Batch:
         if inner_tol is not None:
             opt.inner_tol = inner_tol
         opt.autotune = 1 if autotune else 0
+        opt.test_inject = INJECT[test_inject]
         h = C.c_void_p()
         _check(self.lib.tsfcde_batch_setup(C.byref(h), len(problems), arr, self.M, C.byref(opt)),
                "tsfcde_batch_setup")
@@ -385,11 +413,18 @@ class Batch:
         return {"budget": bud.value, "n1_ge_n2": bool(big.value), "ctas": ctas.value,
                 "best_ms": ms.value}
 
-    def get_level(self, i: int):
-        out = np.empty(self.n[i])
+    def level(self) -> int:
+        """The batch's current level."""
         j = C.c_int64()
-        _check(self.lib.tsfcde_batch_get_level(self.h, i, _dptr(out), C.byref(j)), "tsfcde_batch_get_level")
-        return out, j.value
+        _check(self.lib.tsfcde_batch_level(self.h, C.byref(j)), "tsfcde_batch_level")
+        return j.value
+
+    def get_level(self, i: int, j: Optional[int] = None):
+        """(u^j of instance i, j) for any j <= the current level (default: the current level)."""
+        j = self.level() if j is None else int(j)
+        out = np.empty(self.n[i])
+        _check(self.lib.tsfcde_batch_get_level(self.h, i, j, _dptr(out)), "tsfcde_batch_get_level")
+        return out, j
 
     def history(self, i: int, count: int):
         it = np.zeros(count, dtype=np.int32)

@@ -31,6 +31,10 @@ struct tsfcde_ctx {
   std::vector<double> u0;
   double *omega = nullptr, *gtmp = nullptr;
   double *u0dev = nullptr;   // device copy of phi(x_i), for tsfcde_reset(ctx, NULL)
+  double *u0march = nullptr; // device copy of u^0 of the current march (tsfcde_get_level)
+  // host samples of the callbacks, taken before any device work (tsfcde_setup)
+  std::vector<double> gam_h, dp_h, dm_h, f_h, src_x_h, src_t_h;
+  std::vector<int> newsym_h;
   double2 *BhF = nullptr;
   double *gam = nullptr, *dp = nullptr, *dm = nullptr;
   bool own_stream = true;
@@ -182,41 +186,61 @@ void tsfcde_free(tsfcde_ctx *c) {
   delete c;
 }
 
-static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus,
-                      tsfcde_coef_fn d_minus, tsfcde_field_fn phi, tsfcde_field_fn f, void *user) {
+// Every callback sampled on the host at the mesh of Section 2.1 (x_i = a + i h, t_{j+sigma} =
+// (j + sigma) tau), and every host-side check, before any device work: a NaN from a callback or a
+// negative diffusion coefficient is reported without touching the GPU.
+static int sample_host(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus,
+                       tsfcde_coef_fn d_minus, tsfcde_field_fn phi, tsfcde_field_fn f, void *user) {
   const int64_t n = c->n, M = c->M;
-  // ---- host tables: callbacks at t_{j+sigma} (Eq. (2.1)) ----
-  std::vector<double> xg(n), gam(M), dp(M), dm(M);
+  std::vector<double> xg(n);
   for (int64_t i = 0; i < n; ++i) xg[i] = c->a + (double)(i + 1) * c->h;
   c->u0.assign(n, 0.0);
   phi(0.0, xg.data(), c->u0.data(), n, user);
   if (!all_finite(c->u0.data(), n)) return TSFCDE_E_NONFINITE;
-  std::vector<int> newsym(M, 0);
+  c->gam_h.assign(M, 0.0);
+  c->dp_h.assign(M, 0.0);
+  c->dm_h.assign(M, 0.0);
+  c->newsym_h.assign(M, 0);
+  std::vector<double> ts(M);
   for (int64_t j = 0; j < M; ++j) {
     const double t = ((double)j + c->sigma) * c->tau;
-    gam[j] = gamma(t, user);
-    dp[j] = d_plus(t, user);
-    dm[j] = d_minus(t, user);
-    if (!std::isfinite(gam[j]) || !std::isfinite(dp[j]) || !std::isfinite(dm[j])) return TSFCDE_E_NONFINITE;
-    if (dp[j] < 0.0 || dm[j] < 0.0) return TSFCDE_E_INVALID_ARG;
-    newsym[j] = (j <= 1) || gam[j] != gam[j - 1] || dp[j] != dp[j - 1] || dm[j] != dm[j - 1];
+    ts[j] = t;
+    c->gam_h[j] = gamma(t, user);
+    c->dp_h[j] = d_plus(t, user);
+    c->dm_h[j] = d_minus(t, user);
+    if (!std::isfinite(c->gam_h[j]) || !std::isfinite(c->dp_h[j]) || !std::isfinite(c->dm_h[j]))
+      return TSFCDE_E_NONFINITE;
+    if (c->dp_h[j] < 0.0 || c->dm_h[j] < 0.0) return TSFCDE_E_INVALID_ARG;
+    c->newsym_h[j] = (j <= 1) || c->gam_h[j] != c->gam_h[j - 1] || c->dp_h[j] != c->dp_h[j - 1] ||
+                     c->dm_h[j] != c->dm_h[j - 1];
     // Algorithm "... with constant coefficients" needs one level matrix for every j >= 1
-    if (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && j >= 2 && newsym[j]) return TSFCDE_E_INVALID_ARG;
+    if (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && j >= 2 && c->newsym_h[j]) return TSFCDE_E_INVALID_ARG;
+  }
+  if (f) {
+    c->f_h.resize((size_t)M * n);
+    for (int64_t j = 0; j < M; ++j) f(ts[j], xg.data(), c->f_h.data() + (size_t)j * n, n, user);
+    if (!all_finite(c->f_h.data(), c->f_h.size())) return TSFCDE_E_NONFINITE;
   }
   const int R = c->opt.source_rank;
-  std::vector<double> fdense;
-  if (f) {
-    fdense.resize((size_t)M * n);
-    for (int64_t j = 0; j < M; ++j) {
-      const double t = ((double)j + c->sigma) * c->tau;
-      f(t, xg.data(), fdense.data() + (size_t)j * n, n, user);
-    }
-    if (!all_finite(fdense.data(), fdense.size())) return TSFCDE_E_NONFINITE;
-  }
   if (R > 0) {
-    if (!all_finite(c->opt.source_x, (size_t)R * n) || !all_finite(c->opt.source_t, (size_t)R * M))
+    c->src_x_h.assign((size_t)R * n, 0.0);
+    c->src_t_h.assign((size_t)R * M, 0.0);
+    for (int r = 0; r < R; ++r) {
+      if (!c->opt.source_space[r] || !c->opt.source_time[r]) return TSFCDE_E_INVALID_ARG;
+      c->opt.source_space[r](0.0, xg.data(), c->src_x_h.data() + (size_t)r * n, n, user);
+      for (int64_t j = 0; j < M; ++j) c->src_t_h[(size_t)r * M + j] = c->opt.source_time[r](ts[j], user);
+    }
+    if (!all_finite(c->src_x_h.data(), c->src_x_h.size()) || !all_finite(c->src_t_h.data(), c->src_t_h.size()))
       return TSFCDE_E_NONFINITE;
   }
+  return TSFCDE_OK;
+}
+
+static int setup_impl(tsfcde_ctx *c, bool has_f) {
+  const int64_t n = c->n, M = c->M;
+  const std::vector<double> &gam = c->gam_h, &dp = c->dp_h, &dm = c->dm_h;
+  const std::vector<int> &newsym = c->newsym_h;
+  const int R = c->opt.source_rank;
 
   // ---- plans ----
   Args &A = c->A;
@@ -249,6 +273,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
   A.spin_limit = 1ll << c->opt.barrier_spin_log2;
   A.test_skip = 0;
   A.gsf = (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && M >= 2) ? 1 : 0;
+  A.inject = 0;   // the device-side testing hooks are armed once setup has finished
   const bool mixed = A.precision == TSFCDE_MIXED;
 
   // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
@@ -340,6 +365,7 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     c->omega = cv.take<double>(n + 2);
     c->gtmp = cv.take<double>(n + 2);
     c->u0dev = cv.take<double>(n);
+    c->u0march = cv.take<double>(n);
     A.outer_iters = cv.take<int>(M);
     A.escalated = cv.take<int>(M);
     if (mixed) {
@@ -382,11 +408,12 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
       A.SR0 = cv.take<double2>(N + 1);
       A.Y3 = cv.take<double2>(N);
     }
-    A.f_dense = f ? cv.take<double>((size_t)M * n) : nullptr;
+    A.f_dense = has_f ? cv.take<double>((size_t)M * n) : nullptr;
     A.src_x = R > 0 ? cv.take<double>((size_t)R * n) : nullptr;
     A.src_t = R > 0 ? cv.take<double>((size_t)R * M) : nullptr;
     if (!pass) {
       c->arena_bytes = cv.off + 256;
+      if (c->opt.test_inject == TSFCDE_INJECT_NOMEM) return TSFCDE_E_NOMEM;   // testing hook
       CK(cudaMalloc(&c->arena, c->arena_bytes));
       CK(cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream));
     }
@@ -419,17 +446,18 @@ static int setup_impl(tsfcde_ctx *c, tsfcde_coef_fn gamma, tsfcde_coef_fn d_plus
     CK(cudaMemcpyAsync((void *)A.lv_inner, c->lv_inner.data(), M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync((void *)A.lv_floor, c->lv_floor.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   }
-  if (f)
-    CK(cudaMemcpyAsync((void *)A.f_dense, fdense.data(), fdense.size() * sizeof(double),
+  if (has_f)
+    CK(cudaMemcpyAsync((void *)A.f_dense, c->f_h.data(), c->f_h.size() * sizeof(double),
                        cudaMemcpyHostToDevice, c->stream));
   if (R > 0) {
-    CK(cudaMemcpyAsync((void *)A.src_x, c->opt.source_x, (size_t)R * n * sizeof(double),
+    CK(cudaMemcpyAsync((void *)A.src_x, c->src_x_h.data(), (size_t)R * n * sizeof(double),
                        cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync((void *)A.src_t, c->opt.source_t, (size_t)R * M * sizeof(double),
+    CK(cudaMemcpyAsync((void *)A.src_t, c->src_t_h.data(), (size_t)R * M * sizeof(double),
                        cudaMemcpyHostToDevice, c->stream));
   }
   CK(cudaMemcpyAsync(A.u, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->u0dev, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->u0march, c->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 
   // ---- device setup: weights (Lemma 2), time tables (Lemma 1), spectra ----
   int st = tsf::launch_weights(c->omega, c->gtmp, (int)n, c->beta, c->stream);
@@ -521,15 +549,15 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
   if (opt) o = *opt;
   if (o.preconditioner < 0 || o.preconditioner > 2 ||
       (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1 ||
-      o.source_rank < 0 || (o.source_rank > 0 && (!o.source_x || !o.source_t || f)))
+      o.source_rank < 0 || o.source_rank > 64 ||
+      (o.source_rank > 0 && (!o.source_space || !o.source_time || f)))
     return TSFCDE_E_INVALID_ARG;
   if (o.precision == TSFCDE_MIXED && (!(o.inner_tol > 0 && o.inner_tol < 1) || o.inner_maxit < 1 || o.outer_maxit < 1))
     return TSFCDE_E_INVALID_ARG;
   if (o.barrier_spin_log2 < 8 || o.barrier_spin_log2 > 40) return TSFCDE_E_INVALID_ARG;
   if (o.inner_precision < 0 || o.inner_precision > 2) return TSFCDE_E_INVALID_ARG;
   if (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST) return TSFCDE_E_INVALID_ARG;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
+  if (o.test_inject < TSFCDE_INJECT_NONE || o.test_inject > TSFCDE_INJECT_SINGULAR) return TSFCDE_E_INVALID_ARG;
   tsfcde_ctx *c = new tsfcde_ctx();
   c->device = o.device;
   c->opt = o;
@@ -543,6 +571,19 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
   c->h = (b - a) / (double)(N + 1);
   c->tau = T / (double)M;
   c->sigma = 1.0 - alpha / 2.0;
+  // callbacks on the host first: their errors need no device
+  int st = sample_host(c, gamma, d_plus, d_minus, phi, f, user);
+  if (st != TSFCDE_OK) {
+    delete c;
+    return st;
+  }
+  c->opt.source_space = nullptr;   // the callback arrays are not kept past setup
+  c->opt.source_time = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) {
+    delete c;
+    return TSFCDE_E_NO_DEVICE;
+  }
   if (cudaSetDevice(c->device) != cudaSuccess) {
     delete c;
     return TSFCDE_E_CUDA;
@@ -558,12 +599,19 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
     tsfcde_free(c);
     return TSFCDE_E_CUDA;
   }
-  const int st = setup_impl(c, gamma, d_plus, d_minus, phi, f, user);
+  st = setup_impl(c, f != nullptr);
+  // host samples are on the device now (or no longer needed)
+  cudaStreamSynchronize(c->stream);
+  std::vector<double>().swap(c->f_h);
+  std::vector<double>().swap(c->src_x_h);
+  std::vector<double>().swap(c->src_t_h);
   if (st != TSFCDE_OK) {
     tsfcde_free(c);
     return st;
   }
   c->A.test_skip = o.test_skip_arrival ? 1 : 0;
+  c->A.inject = (o.test_inject == TSFCDE_INJECT_BREAKDOWN || o.test_inject == TSFCDE_INJECT_SINGULAR)
+                    ? o.test_inject : 0;
   *out = c;
   return TSFCDE_OK;
 }
@@ -588,7 +636,8 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     } else {
       st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e, c->march_threads);
     }
-    c->A.test_skip = 0;   // the testing hook applies to one launch only
+    c->A.test_skip = 0;   // the testing hooks apply to one launch only
+    c->A.inject = 0;
     if (st) return st;
     CK(cudaEventRecord(c->ev1, c->stream));
     ++launches;
@@ -639,14 +688,35 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
   return worst;
 }
 
-int tsfcde_get_level(tsfcde_ctx *c, double *u_out, int64_t *level) {
+int tsfcde_get_level(tsfcde_ctx *c, int64_t j, double *u_out) {
+  if (!c || !u_out || j < 0 || j > c->level) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  if (j == c->level) {
+    CK(cudaMemcpyAsync(u_out, c->A.u, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    // H is rewritten by every level before use, so it serves as the output here
+    const int st = tsf::launch_level_rebuild(c->u0march, c->A.u, c->A.ring, c->A.ring_stride, (int)c->n,
+                                             (int)j, (int)c->level, c->A.H, c->stream);
+    if (st) return st;
+    CK(cudaMemcpyAsync(u_out, c->A.H, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return TSFCDE_OK;
+}
+
+int tsfcde_level(tsfcde_ctx *c, int64_t *level) {
+  if (!c || !level) return TSFCDE_E_INVALID_ARG;
+  *level = c->level;
+  return TSFCDE_OK;
+}
+
+int tsfcde_get_weights(tsfcde_ctx *c, double *g_out, double *omega_out) {
   if (!c) return TSFCDE_E_INVALID_ARG;
   CK(cudaSetDevice(c->device));
-  if (level) *level = c->level;
-  if (u_out) {
-    CK(cudaMemcpyAsync(u_out, c->A.u, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-  }
+  const size_t bytes = (size_t)(c->n + 2) * sizeof(double);
+  if (g_out) CK(cudaMemcpyAsync(g_out, c->gtmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (omega_out) CK(cudaMemcpyAsync(omega_out, c->omega, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return TSFCDE_OK;
 }
 
@@ -654,7 +724,8 @@ int tsfcde_solve(tsfcde_ctx *c, double *u_out, tsfcde_stats *stats) {
   if (!c) return TSFCDE_E_INVALID_ARG;
   const int st = tsfcde_step(c, c->M - c->level, stats);
   if (st != TSFCDE_OK && st != TSFCDE_E_NOT_CONVERGED) return st;
-  const int st2 = tsfcde_get_level(c, u_out, nullptr);
+  if (!u_out) return st;
+  const int st2 = tsfcde_get_level(c, c->level, u_out);
   return st2 ? st2 : st;
 }
 
@@ -667,6 +738,7 @@ int tsfcde_reset(tsfcde_ctx *c, const double *u0) {
   } else {
     CK(cudaMemcpyAsync(c->A.u, c->u0dev, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   }
+  CK(cudaMemcpyAsync(c->u0march, c->A.u, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->level = 0;
   return TSFCDE_OK;

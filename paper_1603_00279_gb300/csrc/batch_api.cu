@@ -30,6 +30,7 @@ struct tsfcde_batch {
   int *d_order = nullptr;
   unsigned *d_next = nullptr;
   double *d_u0 = nullptr;            // all instances' u^0, concatenated (N_i doubles each)
+  std::vector<double> u0_h;          // phi of every instance sampled on its mesh (host, setup only)
   double *d_uout = nullptr;          // staging for tsfcde_batch_get_all (same layout)
   // per-instance status words and per-level histories, contiguous over instances so that one
   // copy reads them all: status K x 4, iters / resid / outer / escalated K x M
@@ -341,6 +342,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     b->d_uout = cv.take<double>(u0_total);
     b->u_total = u0_total;
     if (!pass) {
+      if (b->opt.test_inject == TSFCDE_INJECT_NOMEM) return TSFCDE_E_NOMEM;   // testing hook
       CK(cudaMalloc(&b->arena, cv.off + 256));
       CK(cudaMemsetAsync(b->arena, 0, cv.off + 256, b->stream));
     }
@@ -405,7 +407,7 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     }
   }
   // ---- setup inputs, order (largest first), uploads ----
-  std::vector<double> u0all(u0_total);
+  const std::vector<double> &u0all = b->u0_h;
   for (int64_t i = 0; i < K; ++i) {
     const tsfcde_instance &I = in[i];
     tsf::InstanceSetup &S = setup[i];
@@ -416,7 +418,6 @@ static int batch_setup_impl(tsfcde_batch *b, const tsfcde_instance *in) {
     S.gamma = I.gamma;
     S.d_plus = I.d_plus;
     S.d_minus = I.d_minus;
-    std::memcpy(u0all.data() + b->u0_off[i], I.u0, (size_t)I.N * sizeof(double));
   }
   std::vector<int> order(K);
   std::iota(order.begin(), order.end(), 0);
@@ -476,18 +477,33 @@ int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance 
       (o.precision != TSFCDE_FP64 && o.precision != TSFCDE_MIXED) || !(o.tol > 0) || o.maxit < 1 ||
       (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST))
     return TSFCDE_E_INVALID_ARG;
+  if (o.test_inject != TSFCDE_INJECT_NONE && o.test_inject != TSFCDE_INJECT_NOMEM) return TSFCDE_E_INVALID_ARG;
+  size_t total = 0;
   for (int64_t i = 0; i < count; ++i) {
     const tsfcde_instance &I = inst[i];
     if (!(I.a < I.b) || !(I.T > 0) || I.N < 1 || I.N > 16383 || !(I.alpha > 0 && I.alpha <= 1) ||
-        !(I.beta > 1 && I.beta <= 2) || !(I.d_plus >= 0) || !(I.d_minus >= 0) || !I.u0 ||
+        !(I.beta > 1 && I.beta <= 2) || !(I.d_plus >= 0) || !(I.d_minus >= 0) || !I.phi ||
         !std::isfinite(I.gamma))
       return TSFCDE_E_INVALID_ARG;
+    total += (size_t)I.N;
+  }
+  // u^0_i = phi(x_i) on each instance's mesh x_i = a + i h (Section 2.1), before any device work
+  std::vector<double> u0h(total), xg;
+  size_t off = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const tsfcde_instance &I = inst[i];
+    const double h = (I.b - I.a) / (double)(I.N + 1);
+    xg.resize(I.N);
+    for (int64_t k = 0; k < I.N; ++k) xg[k] = I.a + (double)(k + 1) * h;
+    I.phi(0.0, xg.data(), u0h.data() + off, I.N, I.user);
     for (int64_t k = 0; k < I.N; ++k)
-      if (!std::isfinite(I.u0[k])) return TSFCDE_E_NONFINITE;
+      if (!std::isfinite(u0h[off + k])) return TSFCDE_E_NONFINITE;
+    off += (size_t)I.N;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o.device || o.device < 0) return TSFCDE_E_NO_DEVICE;
   tsfcde_batch *b = new tsfcde_batch();
+  b->u0_h.swap(u0h);
   b->device = o.device;
   b->opt = o;
   b->count = count;
@@ -508,6 +524,8 @@ int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance 
     return TSFCDE_E_CUDA;
   }
   const int st = batch_setup_impl(b, inst);
+  cudaStreamSynchronize(b->stream);   // the host samples are on the device (or no longer needed)
+  std::vector<double>().swap(b->u0_h);
   if (st != TSFCDE_OK) {
     tsfcde_batch_free(b);
     return st;
@@ -652,14 +670,27 @@ int tsfcde_batch_step(tsfcde_batch *b, int64_t nsteps, tsfcde_stats *stats) {
   return worst;
 }
 
-int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, double *u_out, int64_t *level) {
-  if (!b || i < 0 || i >= b->count) return TSFCDE_E_INVALID_ARG;
+int tsfcde_batch_get_level(tsfcde_batch *b, int64_t i, int64_t j, double *u_out) {
+  if (!b || !u_out || i < 0 || i >= b->count || j < 0 || j > b->level) return TSFCDE_E_INVALID_ARG;
   CK(cudaSetDevice(b->device));
-  if (level) *level = b->level;
-  if (u_out) {
-    CK(cudaMemcpyAsync(u_out, b->inst[i].u, b->n[i] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
+  const Args &A = b->inst[i];
+  if (j == b->level) {
+    CK(cudaMemcpyAsync(u_out, A.u, b->n[i] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  } else {
+    // the get_all staging area of this instance holds the rebuilt level
+    double *tmp = b->d_uout + b->u0_off[i];
+    const int st = tsf::launch_level_rebuild(b->d_u0 + b->u0_off[i], A.u, A.ring, A.ring_stride, A.n, (int)j,
+                                             (int)b->level, tmp, b->stream);
+    if (st) return st;
+    CK(cudaMemcpyAsync(u_out, tmp, b->n[i] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
   }
+  CK(cudaStreamSynchronize(b->stream));
+  return TSFCDE_OK;
+}
+
+int tsfcde_batch_level(tsfcde_batch *b, int64_t *level) {
+  if (!b || !level) return TSFCDE_E_INVALID_ARG;
+  *level = b->level;
   return TSFCDE_OK;
 }
 

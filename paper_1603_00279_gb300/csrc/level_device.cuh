@@ -134,6 +134,16 @@ struct LevelScalars {
 __device__ __forceinline__ double l21_a(double alpha, double sigma, int l);
 __device__ __forceinline__ double l21_b(double alpha, double sigma, int l);
 
+// lambda_1, lambda_0, lambda_{-1} of Lemma 2, each operation rounded on its own (no contraction
+// into fused multiply-adds), in the order the formulas are written: the weights then round
+// exactly as a plain binary64 evaluation of Lemma 2 does on any conforming host.
+__device__ __forceinline__ void wsgd_lambdas(double beta, double &lam1, double &lam0, double &lamm1) {
+  const double bb = __dmul_rn(beta, beta), b3 = __dmul_rn(3.0, beta);
+  lam1 = __ddiv_rn(__dadd_rn(__dadd_rn(bb, b3), 2.0), 12.0);
+  lam0 = __ddiv_rn(__dsub_rn(4.0, bb), 6.0);
+  lamm1 = __ddiv_rn(__dadd_rn(__dsub_rn(bb, b3), 2.0), 12.0);
+}
+
 __device__ __forceinline__ LevelScalars level_scalars(const Args &A, int j) {
   LevelScalars s;
   s.eta = A.lv_eta[j];
@@ -360,21 +370,74 @@ __device__ __forceinline__ void st2(double *v, int m, double2 z) { reinterpret_c
 // phases of the level symbols
 // ------------------------------------------------------------------------------------------------
 
-// Bluestein, inverse n-point DFT of 1/Lambda_P (first column of P^{-1}), phase 1 of 3.
+// Deterministic block min and max (fixed shuffle tree, fixed warp order); every thread gets both.
+__device__ __forceinline__ void block_minmax(double &mn, double &mx, double *sm /* 64 doubles */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    sm[w] = mn;
+    sm[32 + w] = mx;
+  }
+  __syncthreads();
+  mn = sm[0];
+  mx = sm[32];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+    mn = fmin(mn, sm[i]);
+    mx = fmax(mx, sm[32 + i]);
+  }
+  __syncthreads();
+}
+
+// Bluestein, inverse n-point DFT of 1/Lambda_P (first column of P^{-1}), phase 1 of 3.  Also the
+// smallest and largest |Lambda_P|^2 of this CTA's frequencies, into slot 3 of its partials records
+// (buffer 0: min, buffer 1: max; the CGS reductions use slots 0-2 only).
 static __device__ void ph_pinv_b1(const Args &A, const Smem &S, int j) {
   const LevelScalars s = level_scalars(A, j);
   const int n = A.n;
+  double dmin = INFINITY, dmax = 0.0;
   col_pass<false, true, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, nullptr, A.Y1,
                                  [&](int m, double2) -> double2 {
                                    if (m >= n) return make_double2(0.0, 0.0);
                                    const double2 lp = lambda_p(A, s, m);
-                                   const double d = lp.x * lp.x + lp.y * lp.y;
-                                   if (!(d > 0.0) || !isfinite(d)) raise_fatal(A, kESingular);
+                                   double d = lp.x * lp.x + lp.y * lp.y;
+                                   if (A.inject == 3 && m == 0) d = 0.0;   // testing hook
+                                   if (!(d > 0.0) || !isfinite(d)) {
+                                     raise_fatal(A, kESingular);
+                                     return make_double2(0.0, 0.0);
+                                   }
+                                   dmin = fmin(dmin, d);
+                                   dmax = fmax(dmax, d);
                                    const double2 inv = make_double2(lp.x / d, -lp.y / d);
                                    return cmul(inv, A.chirpI[m]);
                                  });
+  block_minmax(dmin, dmax, S.red);
+  if (threadIdx.x == 0) {
+    const int cnt = team().cnt, idx = team().idx;
+    A.partials[((size_t)0 * cnt + idx) * 4 + 3] = dmin;
+    A.partials[((size_t)1 * cnt + idx) * 4 + 3] = dmax;
+  }
 }
-static __device__ void ph_pinv_b2(const Args &A, const Smem &S) { crow_pass<0>(A, S, A.BhI, nullptr, 1.0); }
+// Bluestein phase 2 of 3, after the check that P is numerically nonsingular: its eigenvalues
+// must satisfy min |Lambda_P| > 1e3 u64 max |Lambda_P| (Theorem 4 proves nonsingularity only for
+// beta above about 1.6168; below that the check stands in for it).
+constexpr double kSingRel2 = (1e3 * 1.1102230246251565e-16) * (1e3 * 1.1102230246251565e-16);
+static __device__ void ph_pinv_b2(const Args &A, const Smem &S) {
+  if (team().idx == 0 && threadIdx.x == 0) {
+    const int cnt = team().cnt;
+    double mn = INFINITY, mx = 0.0;
+    for (int b = 0; b < cnt; ++b) {
+      mn = fmin(mn, A.partials[(size_t)b * 4 + 3]);
+      mx = fmax(mx, A.partials[((size_t)cnt + b) * 4 + 3]);
+    }
+    if (!(mn > kSingRel2 * mx)) raise_fatal(A, kESingular);
+  }
+  crow_pass<0>(A, S, A.BhI, nullptr, 1.0);
+}
 static __device__ void ph_pinv_b3(const Args &A, const Smem &S) {
   const int n = A.n;
   col_pass<true, false, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
@@ -589,7 +652,7 @@ __device__ int cgs_solve(const Args &A, const Smem &S, const Krylov<T> &V, doubl
     if (!(alive = grid_sync(A))) return kOK;
     read_partials(A, S, rb, tot);
     rb ^= 1;
-    const double sig = tot[0];
+    const double sig = A.inject == 2 ? 0.0 : tot[0];   // testing hook: (r~, v^) = 0
     if (sig == 0.0) return kEBreakdown;
     if (!(sig == sig) || isinf(sig)) return kENonFinite;
     const R alpha = (R)(rho / sig);
@@ -1269,9 +1332,8 @@ static __device__ void instance_tables(const Args &A, double *omega, double *gtm
     }
   }
   __syncthreads();
-  const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
-  const double lam0 = (4.0 - beta * beta) / 6.0;
-  const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+  double lam1, lam0, lamm1;
+  wsgd_lambdas(beta, lam1, lam0, lamm1);
   for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) {
     double w = __dmul_rn(lam1, gtmp[k]);
     if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, gtmp[k - 1]));

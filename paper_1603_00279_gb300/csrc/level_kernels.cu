@@ -29,6 +29,33 @@ __global__ void __launch_bounds__(kThreads, 1) history_kernel(Args A, int j) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// level u^j of a march from its u^0, current level u^c and ring of increments d^s = u^{s+1} - u^s
+// (s < c): the shorter of u^0 + sum_{s<j} d^s and u^c - sum_{j<=s<c} d^s, summed in order of s
+// (coalesced over i; one ring row per term)
+// ------------------------------------------------------------------------------------------------
+__global__ void level_rebuild_kernel(const double *u0, const double *uc, const double *ring,
+                                     long long stride, int n, int j, int c, double *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v;
+    if (j <= c - j) {
+      v = u0[i];
+      for (int s = 0; s < j; ++s) v += ring[(long long)s * stride + i];
+    } else {
+      v = uc[i];
+      for (int s = c - 1; s >= j; --s) v -= ring[(long long)s * stride + i];
+    }
+    out[i] = v;
+  }
+}
+
+int launch_level_rebuild(const double *u0, const double *uc, const double *ring, long long stride, int n,
+                         int j, int c, double *out, cudaStream_t st) {
+  const int blocks = std::min((n + kThreads - 1) / kThreads, 4 * kMaxGrid);
+  level_rebuild_kernel<<<blocks, kThreads, 0, st>>>(u0, uc, ring, stride, n, j, c, out);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+}
+
+// ------------------------------------------------------------------------------------------------
 // diagnostic products y = op_j x (op 0: A, 1: B, 2: P^{-1}, 3: A^{-1} by the Gohberg-Semencul
 // formula); x and y are padded device vectors.
 // ------------------------------------------------------------------------------------------------
@@ -96,9 +123,8 @@ __global__ void grunwald_kernel(double *g, const double *f, int K) {
 }
 
 __global__ void wsgd_kernel(const double *g, double *omega, int K, double beta) {
-  const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
-  const double lam0 = (4.0 - beta * beta) / 6.0;
-  const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+  double lam1, lam0, lamm1;
+  wsgd_lambdas(beta, lam1, lam0, lamm1);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
     double w = __dmul_rn(lam1, g[k]);
     if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, g[k - 1]));
@@ -273,9 +299,8 @@ static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, do
   }
   if (!grid_sync(A)) return;
   {
-    const double lam1 = (beta * beta + 3.0 * beta + 2.0) / 12.0;
-    const double lam0 = (4.0 - beta * beta) / 6.0;
-    const double lamm1 = (beta * beta - 3.0 * beta + 2.0) / 12.0;
+    double lam1, lam0, lamm1;
+    wsgd_lambdas(beta, lam1, lam0, lamm1);
     for (int k = gt; k <= n + 1; k += gs) {
       double w = __dmul_rn(lam1, gtmp[k]);
       if (k >= 1) w = __dadd_rn(w, __dmul_rn(lam0, gtmp[k - 1]));
@@ -309,7 +334,8 @@ static_operator_kernel(tsf::Args A, double *omega, double *gtmp, double beta, do
     for (int sl = gt; sl <= P.N; sl += gs) {
       const int k = sl == P.N ? P.N : ((sl & (P.N2 - 1)) * P.N1 + (sl >> P.lg2));
       double2 sa, sb;
-      ab_symbols(A, s, __ldg(A.twL + k), sl == P.N, A.What[sl], sa, sb);
+      // twL was written earlier in this launch: a plain (coherent) load, not the read-only path
+      ab_symbols(A, s, A.twL[k], sl == P.N, A.What[sl], sa, sb);
       A.SA[sl] = op == 0 ? sa : sb;
     }
   }

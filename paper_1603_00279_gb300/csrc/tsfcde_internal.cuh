@@ -93,6 +93,7 @@ struct Args {
   int *escalated;         // M: 1 if the level fell back to FP64 CGS
   long long spin_limit;   // polls before a barrier wait gives up
   int test_skip;          // testing hook: CTA 0 skips its first barrier arrival
+  int inject;             // testing hook (tsfcde_options.test_inject): 2 breakdown, 3 singular P
   // float-float inner solve (mixed mode, levels where FP32 cannot resolve the operator)
   const int *lv_inner;    // per level: 0 FP32 inner solve, 1 float-float inner solve
   const double *lv_floor; // per level: FP64 residual accepted once refinement stagnates below it
@@ -512,6 +513,8 @@ const void *level_kernel_cta_ptr();
 const void *level_kernel_wide_ptr();
 const void *history_kernel_ptr();
 int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j);
+int launch_level_rebuild(const double *u0, const double *uc, const double *ring, long long stride, int n,
+                         int j, int c, double *out, cudaStream_t st);
 const void *batch_level_kernel_ptr();
 const void *batch_setup_kernel_ptr();
 int launch_batch(const BatchArgs &B, int grid, size_t smem, cudaStream_t st, int setup, int j0, int j1);

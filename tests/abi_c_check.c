@@ -42,6 +42,28 @@ int main(void) {
   tsfcde_batch_free(NULL);
   if (tsfcde_step(NULL, 1, NULL) != TSFCDE_E_INVALID_ARG) return 5;
   if (tsfcde_batch_step(NULL, 1, NULL) != TSFCDE_E_INVALID_ARG) return 6;
+  {
+    double u[15];
+    int64_t lev = 0;
+    if (tsfcde_get_level(NULL, 0, u) != TSFCDE_E_INVALID_ARG) return 7;
+    if (tsfcde_level(NULL, &lev) != TSFCDE_E_INVALID_ARG) return 8;
+    if (tsfcde_get_weights(NULL, u, u) != TSFCDE_E_INVALID_ARG) return 9;
+    if (tsfcde_batch_get_level(NULL, 0, 0, u) != TSFCDE_E_INVALID_ARG) return 10;
+    if (tsfcde_batch_level(NULL, &lev) != TSFCDE_E_INVALID_ARG) return 11;
+  }
+  /* the separable source is given as callbacks the library samples on its own mesh */
+  {
+    tsfcde_field_fn space[1] = {field};
+    tsfcde_coef_fn time[1] = {coef};
+    tsfcde_default_options(&opt);
+    opt.source_rank = 1;
+    opt.source_space = space;
+    opt.source_time = time;
+    opt.test_inject = TSFCDE_INJECT_NONE;
+    /* a separable source and an f callback together: rejected */
+    st = tsfcde_setup(&ctx, 0.0, 1.0, 1.0, 15, 4, 0.5, 1.5, coef, coef, coef, field, field, NULL, &opt);
+    if (st != TSFCDE_E_INVALID_ARG) return 12;
+  }
   printf("c abi ok\n");
   return 0;
 }

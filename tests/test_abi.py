@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,17 +76,17 @@ def test_invalid_options_rejected_without_device():
     phi = P.FIELD_FN(lambda t, x, out, n, u: None)
     for fields in [dict(algorithm=7), dict(algorithm=-1), dict(precision=3), dict(preconditioner=5),
                    dict(tol=0.0), dict(maxit=0), dict(barrier_spin_log2=2), dict(inner_precision=9),
-                   dict(precision=1, inner_tol=2.0)]:
+                   dict(precision=1, inner_tol=2.0), dict(test_inject=4), dict(test_inject=-1),
+                   dict(source_rank=2)]:
         o = opt_with(**fields)
         ctx = C.c_void_p()
         st = lib.tsfcde_setup(C.byref(ctx), 0.0, 1.0, 1.0, 15, 4, 0.5, 1.5, coef, coef, coef, phi,
                               P.FIELD_FN(), None, C.byref(o))
         assert st == 1, fields
         assert not ctx.value
-    u0 = (C.c_double * 15)()
-    inst = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0,
-                                       C.cast(u0, C.POINTER(C.c_double))))
-    for fields in [dict(algorithm=3), dict(precision=5), dict(maxit=0)]:
+    inst = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0, phi, None))
+    for fields in [dict(algorithm=3), dict(precision=5), dict(maxit=0), dict(test_inject=2),
+                   dict(test_inject=3)]:
         o = opt_with(**fields)
         h = C.c_void_p()
         assert lib.tsfcde_batch_setup(C.byref(h), 1, inst, 4, C.byref(o)) == 1, fields
@@ -148,11 +149,77 @@ def test_empty_and_oversize_problems_rejected_without_device():
         st = lib.tsfcde_setup(C.byref(ctx), 0.0, 1.0, 1.0, N, M, 0.5, 1.5, coef, coef, coef, phi,
                               P.FIELD_FN(), None, C.byref(opt))
         assert st == 1 and not ctx.value, (N, M)
-    u0 = (C.c_double * 20000)()
-    p0 = C.cast(u0, C.POINTER(C.c_double))
     h = C.c_void_p()
     assert lib.tsfcde_batch_setup(C.byref(h), 0, None, 4, C.byref(opt)) == 1
-    big = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 16384, 0.5, 1.5, 0.1, 1.0, 1.0, p0))
+    big = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 16384, 0.5, 1.5, 0.1, 1.0, 1.0, phi, None))
     assert lib.tsfcde_batch_setup(C.byref(h), 1, big, 4, C.byref(opt)) == 1
-    ok = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0, p0))
+    ok = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0, phi, None))
     assert lib.tsfcde_batch_setup(C.byref(h), 1, ok, 0, C.byref(opt)) == 1
+    nophi = (P.Instance * 1)(P.Instance(0.0, 1.0, 1.0, 15, 0.5, 1.5, 0.1, 1.0, 1.0, P.FIELD_FN(), None))
+    assert lib.tsfcde_batch_setup(C.byref(h), 1, nophi, 4, C.byref(opt)) == 1
+
+
+def test_nonfinite_callbacks_rejected_before_any_device_work():
+    """A coefficient, initial value, source or separable-source callback that returns NaN or Inf
+    makes setup return E_NONFINITE (4).  Every callback is sampled on the host, on the library's
+    own mesh, before any CUDA call, so this holds on a machine without a GPU; so does the batch's
+    initial value."""
+    import math
+    import paper_1603_00279_gb300 as P
+    P.load_library()
+    base = dict(a=0.0, b=1.0, T=1.0, N=15, M=4, alpha=0.5, beta=1.5, gamma=lambda t: 0.5,
+                d_plus=lambda t: 1.0, d_minus=lambda t: 1.0, phi=lambda x: x * (1 - x))
+    nan = float("nan")
+    cases = [dict(gamma=lambda t: nan if t > 0.3 else 0.5),
+             dict(d_plus=lambda t: math.inf),
+             dict(d_minus=lambda t: nan),
+             dict(phi=lambda x: x / (x - x[3])),                       # Inf at one node
+             dict(f=lambda x, t: np.where(x > 0.5, nan, 0.0)),
+             dict(separable=[(lambda t: 1.0, lambda x: x), (lambda t: nan, lambda x: x)]),
+             dict(separable=[(lambda t: 1.0, lambda x: np.log(x - 0.5))])]
+    for kw in cases:
+        args = dict(base, **kw)
+        with pytest.raises(P.TsfcdeError) as e:
+            P.Solver(**args)
+        assert e.value.status == 4, kw
+    # a negative diffusion coefficient at some t_{j+sigma} is an argument error, found on the host
+    with pytest.raises(P.TsfcdeError) as e:
+        P.Solver(**dict(base, d_minus=lambda t: 1.0 - 2.0 * t))
+    assert e.value.status == 1
+
+    class Q:
+        a, b, T, n, alpha, beta = 0.0, 1.0, 1.0, 15, 0.5, 1.5
+        gamma = staticmethod(lambda t: 0.1)
+        d_plus = staticmethod(lambda t: 1.0)
+        d_minus = staticmethod(lambda t: 1.0)
+        phi = staticmethod(lambda x: np.where(x > 0.9, nan, x))
+    with pytest.raises(P.TsfcdeError) as e:
+        P.Batch([Q()], 4)
+    assert e.value.status == 4
+
+
+def test_separable_source_sampled_by_the_library_on_its_mesh():
+    """The separable source's callbacks receive the library's mesh: X_r is called once with the N
+    interior nodes x_i = a + i h, T_r once per level at t_{j+sigma} = (j + sigma) tau (Section 2.1
+    and Eq. (2.1)).  Recorded on the host during setup, which then fails with a NaN on purpose so
+    that no device is needed."""
+    import paper_1603_00279_gb300 as P
+    P.load_library()
+    seen_x, seen_t = [], []
+
+    def X(x):
+        seen_x.append(np.array(x))
+        return x
+
+    def T(t):
+        seen_t.append(t)
+        return float("nan") if len(seen_t) == 5 else 1.0
+    a, b, N, M, Tf, alpha = -1.0, 2.0, 11, 5, 0.5, 0.4
+    with pytest.raises(P.TsfcdeError) as e:
+        P.Solver(a, b, Tf, N, M, alpha, 1.5, lambda t: 0.0, lambda t: 1.0, lambda t: 1.0,
+                 lambda x: 0 * x, separable=[(T, X)])
+    assert e.value.status == 4
+    h = (b - a) / (N + 1)
+    assert len(seen_x) == 1 and np.array_equal(seen_x[0], a + h * np.arange(1, N + 1))
+    sigma = 1.0 - alpha / 2.0
+    assert seen_t == [(j + sigma) * (Tf / M) for j in range(M)]

@@ -161,10 +161,17 @@ def test_const_shortest_marches(M):
     """M = 1 has no level j >= 1 (plain CGS only); M = 2 builds the generators for its single
     Gohberg-Semencul level; M = 3 uses them once more."""
     # with tau = T/M this large, eta_j is small and the levels are far worse conditioned than in
-    # the marches above: the bound is 1e-10 or 10 cond(A) times the largest level residual
-    def bound(q, max_res):
-        c = max(np.linalg.cond(O.level_matrices(q, j)[0]) for j in range(min(q.M, 2)))
-        return max(1e-10, 10.0 * c * max_res)
+    # the marches above: the bound is 1e-10, or the forward error the stopping rules allow,
+    # sum_j cond(A_j) rho_j, from the oracle's dense matrices (rho_j = tol for the CGS level 0,
+    # max(tol, 64 u64 ||A||_1 / eta) for the Gohberg-Semencul levels)
+    def bound(q, _unused=None, tol=1e-12):
+        tot = 0.0
+        for j in range(q.M):
+            A = O.level_matrices(q, j)[0]
+            rho = tol if j == 0 else max(tol, 64 * 2.0 ** -53 * np.abs(A).sum(axis=1).max()
+                                         / O.level_scalars(q, j)[0])
+            tot += np.linalg.cond(A) * rho
+        return max(1e-10, tot)
 
     P = solver_module()
     prob = _batch_instance(300, M, idx=1)
