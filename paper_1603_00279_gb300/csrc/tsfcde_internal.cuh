@@ -214,6 +214,108 @@ __device__ __forceinline__ void mkc(double2 &z, double x, double y) { z = make_d
 __device__ __forceinline__ void mkc(float2 &z, float x, float y) { z = make_float2(x, y); }
 
 // ---------------------------------------------------------------------------------------------
+// Butterflies.  FP64 and FP32 use the fused multiply-add form of the radix-2 butterfly
+// (Goedecker's): y0 = a + w b takes two FMAs per component, y1 = a - w b = 2a - y0 one, so a
+// twiddled radix-2 butterfly is 6 FMAs for its 10 flops (against 4 multiplies/FMAs and 4 adds
+// plainly).  A twiddled radix-4 butterfly is built from four of them: with stage twiddles
+// w1 = W^k, w2 = W^2k (W^3k = w1 w2),
+//   c0,1 = a0 +- w2 a2,  d0,1 = a1 +- w2 a3,  y0,2 = c0 +- w1 d0,  y1,3 = c1 +- (-+i w1) d1,
+// 24 FMAs and two twiddle loads per four points.  The untwiddled first stage uses plain adds.
+// Float-float keeps the textbook form (its products are not single FMAs).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void bfly_fma(double2 a, double2 b, double2 w, double2 &y0, double2 &y1) {
+  double tx = __fma_rn(w.x, b.x, a.x);
+  tx = __fma_rn(-w.y, b.y, tx);
+  double ty = __fma_rn(w.x, b.y, a.y);
+  ty = __fma_rn(w.y, b.x, ty);
+  y0 = make_double2(tx, ty);
+  y1 = make_double2(__fma_rn(2.0, a.x, -tx), __fma_rn(2.0, a.y, -ty));
+}
+__device__ __forceinline__ void bfly_fma(float2 a, float2 b, float2 w, float2 &y0, float2 &y1) {
+  float tx = __fmaf_rn(w.x, b.x, a.x);
+  tx = __fmaf_rn(-w.y, b.y, tx);
+  float ty = __fmaf_rn(w.x, b.y, a.y);
+  ty = __fmaf_rn(w.y, b.x, ty);
+  y0 = make_float2(tx, ty);
+  y1 = make_float2(__fmaf_rn(2.f, a.x, -tx), __fmaf_rn(2.f, a.y, -ty));
+}
+
+template <typename T> struct FmaButterfly { static constexpr bool value = false; };
+template <> struct FmaButterfly<double2> { static constexpr bool value = true; };
+template <> struct FmaButterfly<float2> { static constexpr bool value = true; };
+
+// Radix-4 DIT butterfly of Stockham sub-length Ls at position k (stage twiddles from tw[m << sh],
+// tw[m] = e^{-2 pi i m / 2^lgT}; conjugated for SIGN > 0).
+template <int SIGN, typename T>
+__device__ __forceinline__ void radix4(T &a0, T &a1, T &a2, T &a3, const T *tw, int k, int sh, bool first) {
+  if (first) {   // k = 0 throughout the first stage: no twiddles
+    const T b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+    const T b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
+    a0 = cadd(b0, b2);
+    a1 = cadd(b1, b3);
+    a2 = csub(b0, b2);
+    a3 = csub(b1, b3);
+    return;
+  }
+  if constexpr (FmaButterfly<T>::value) {
+    T w1 = tw[k << sh], w2 = tw[(2 * k) << sh];
+    if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); }
+    T c0, c1, d0, d1;
+    bfly_fma(a0, a2, w2, c0, c1);
+    bfly_fma(a1, a3, w2, d0, d1);
+    T v;
+    if (SIGN < 0) mkc(v, w1.y, -w1.x);   // -i w1
+    else mkc(v, -w1.y, w1.x);            // +i w1
+    bfly_fma(c0, d0, w1, a0, a2);
+    bfly_fma(c1, d1, v, a1, a3);
+  } else {
+    if (k) {
+      T w1 = tw[k << sh];
+      T w2 = tw[(2 * k) << sh];
+      T w3 = tw[(3 * k) << sh];
+      if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
+      a1 = cmul(a1, w1);
+      a2 = cmul(a2, w2);
+      a3 = cmul(a3, w3);
+    }
+    const T b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+    const T b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
+    a0 = cadd(b0, b2);
+    a1 = cadd(b1, b3);
+    a2 = csub(b0, b2);
+    a3 = csub(b1, b3);
+  }
+}
+
+// Radix-2 DIT butterfly (the odd last stage of a power-of-two length).
+template <int SIGN, typename T>
+__device__ __forceinline__ void radix2(T &a0, T &a1, const T *tw, int k, int sh, bool first) {
+  if (first) {
+    const T y0 = cadd(a0, a1), y1 = csub(a0, a1);
+    a0 = y0;
+    a1 = y1;
+    return;
+  }
+  if constexpr (FmaButterfly<T>::value) {
+    T w1 = tw[k << sh];
+    if (SIGN > 0) w1 = cconj(w1);
+    T y0, y1;
+    bfly_fma(a0, a1, w1, y0, y1);
+    a0 = y0;
+    a1 = y1;
+  } else {
+    if (k) {
+      T w1 = tw[k << sh];
+      if (SIGN > 0) w1 = cconj(w1);
+      a1 = cmul(a1, w1);
+    }
+    const T y0 = cadd(a0, a1), y1 = csub(a0, a1);
+    a0 = y0;
+    a1 = y1;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Stockham radix-4/2 FFT of `nl` lines of length P = 2^lgP in shared memory.
 // Line l occupies a[l*P .. l*P+P); b is a scratch area of the same size.  SIGN = -1 forward,
 // +1 inverse (unnormalised).  Twiddles come from tw[k] = e^{-2 pi i k / 2^lgT}, 2^lgT >= P
@@ -240,22 +342,12 @@ __device__ __forceinline__ T *smem_fft(T *a, T *b, int lgP, int nl, const T *tw,
         const T *x = a + l * P;
         T *y = b + l * P;
         T a0 = x[j], a1 = x[j + Q], a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
-        if (k) {
-          T w1 = tw[k << sh];
-          T w2 = tw[(2 * k) << sh];
-          T w3 = tw[(3 * k) << sh];
-          if (SIGN > 0) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
-          a1 = cmul(a1, w1);
-          a2 = cmul(a2, w2);
-          a3 = cmul(a3, w3);
-        }
-        const T b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
-        const T b3 = SIGN < 0 ? mul_mi(csub(a1, a3)) : mul_i(csub(a1, a3));
+        radix4<SIGN>(a0, a1, a2, a3, tw, k, sh, lgLs == 0);
         const int base = ((j - k) << 2) + k;
-        y[base] = cadd(b0, b2);
-        y[base + Ls] = cadd(b1, b3);
-        y[base + 2 * Ls] = csub(b0, b2);
-        y[base + 3 * Ls] = csub(b1, b3);
+        y[base] = a0;
+        y[base + Ls] = a1;
+        y[base + 2 * Ls] = a2;
+        y[base + 3 * Ls] = a3;
       }
       lgLs += 2;
     } else {
@@ -269,14 +361,10 @@ __device__ __forceinline__ T *smem_fft(T *a, T *b, int lgP, int nl, const T *tw,
         const T *x = a + l * P;
         T *y = b + l * P;
         T a0 = x[j], a1 = x[j + Q];
-        if (k) {
-          T w1 = tw[k << sh];
-          if (SIGN > 0) w1 = cconj(w1);
-          a1 = cmul(a1, w1);
-        }
+        radix2<SIGN>(a0, a1, tw, k, sh, lgLs == 0);
         const int base = ((j - k) << 1) + k;
-        y[base] = cadd(a0, a1);
-        y[base + Ls] = csub(a0, a1);
+        y[base] = a0;
+        y[base + Ls] = a1;
       }
       lgLs += 1;
     }
