@@ -499,6 +499,8 @@ def run_native(args, p):
                 "ms": hms, "fp64_tflops": 2.0 * n * jh / (hms / 1e3) / 1e12,
                 "peak_source": peak[1]}
 
+    fp64_measured = P.measure_fp64(local)    # the FP64 unit's FMA throughput, measured now
+
     # end to end through the C ABI with pinned host buffers: H2D of u^0, the march, D2H of u^M;
     # u^0 is the library's own sample of phi on its mesh (level 0 read back after a reset)
     s.reset()
@@ -563,6 +565,7 @@ def run_native(args, p):
     clocks = clk.summary()
     traffic, tsrc = captured_traffic(args.traffic_profile) if lpl == 64 else (None, "launch shape differs from the capture")
     rl = roofline("level_kernel", flops / launches_per_step, kernel_ms / launches_per_step, args.precision)
+    rl["fp64_fma_measured_tflops"] = fp64_measured
     rl["traffic"] = traffic
     rl["traffic_source"] = tsrc
     rl["per"] = f"launch ({lpl or M} levels; {launches_per_step:.0f} launches per march)"
@@ -738,9 +741,11 @@ def run_native_batch(args, probs_all):
 
 
 def run_native_history(args, probs):
-    """History-dominated workload: instances of n = 2^18-1, M = 8192 marched one after another
-    (each holds a 17 GB FP64 history), FP64 history accumulation, the given precision for the
-    solves."""
+    """History-dominated workload: instances of n = 2^18-1, M = 8192 (each holds a 17 GB FP64
+    history ring, plus 34 GB of block spectra with fast history), FP64 history accumulation, the
+    given precision for the solves.  The instances are set up in groups that fit the device's free
+    memory; each group is warmed up and its timed marches are added to the step time (setup is
+    outside the timed region).  One step marches every instance once."""
     import torch
     ranks = Ranks().init()
     from paper_1603_00279_gb300 import build
@@ -752,83 +757,125 @@ def run_native_history(args, probs):
     probs_all = probs
     probs = shard_instances(probs_all, ranks)
     ntot = sum(q.n * q.M for q in probs_all)
-    ctxs = [P.Solver.from_problem(q, source="separable", stream=stream.cuda_stream,
-                                  precision=args.precision, maxit=args.maxit) for q in probs]
+    fast = args.fast_history != "off"
+    q0 = probs[0]
+    stride = (q0.n + 31) // 32 * 32
+    per_inst = 8 * stride * q0.M + 40 * 8 * 2 * stride
+    if fast:
+        per_inst += 16 * 129 * ((q0.M - 1) // 128) * stride + 8 * 128 * stride
+    free = torch.cuda.mem_get_info()[0]
+    G = max(1, min(len(probs), int(0.85 * free // per_inst)))
+    groups = [list(range(i, min(len(probs), i + G))) for i in range(0, len(probs), G)]
 
-    def one_step():
-        out = []
-        for q, s in zip(probs, ctxs):
-            s.reset()
-            out.append(s.step(q.M))
-        return out
+    def make(q):
+        return P.Solver.from_problem(q, source="separable", stream=stream.cuda_stream,
+                                     precision=args.precision, maxit=args.maxit,
+                                     fast_history=fast, autotune=not args.no_autotune)
 
-    for _ in range(args.warmup):
-        one_step()
-    ranks.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(ranks.local) as clk:
-        e0.record(stream)
-        stats = [one_step() for _ in range(args.steps)]
-        e1.record(stream)
+    ms_total = 0.0
+    stats = []           # per timed step: the stats of every instance
+    errs = [None] * len(probs)
+    launches = 0
+    hist = e2e = None
+    flops = 0.0
+    kernel_ms = 0.0
+    samples = []
+    for gi, grp in enumerate(groups):
+        ctxs = [make(probs[i]) for i in grp]
+        for _ in range(args.warmup):
+            for i, s in zip(grp, ctxs):
+                s.reset()
+                s.step(probs[i].M)
+        ranks.barrier()
         torch.cuda.synchronize()
-    ranks.barrier()
-    ms = ranks.max(e0.elapsed_time(e1))
-    # history phase at the last level of the first instance
-    q0, s0 = probs[0], ctxs[0]
-    jh = q0.M - 1
-    s0.history_sum(jh, want=False)
-    h0 = torch.cuda.Event(enable_timing=True)
-    h1 = torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    for _ in range(3):
-        s0.history_sum(jh, want=False)
-    h1.record(stream)
-    torch.cuda.synchronize()
-    hms = h0.elapsed_time(h1) / 3
-    hbytes = 8.0 * q0.n * jh + 16.0 * q0.n
-    peak = hbm_peak()
-    errs = []
-    for q, s in zip(probs, ctxs):
-        u, _ = s.get_level()
-        errs.append(float(np.sqrt(q.h) * np.linalg.norm(u - q.exact(q.grid(), q.T))))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(ranks.local) as clk:
+            e0.record(stream)
+            gstats = []
+            for _ in range(args.steps):
+                row = []
+                for i, s in zip(grp, ctxs):
+                    s.reset()
+                    row.append(s.step(probs[i].M))
+                gstats.append(row)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        samples += clk.lines if hasattr(clk, "lines") else []
+        stats.append(gstats)
+        launches += int(sum(st["device_launches"] for row in gstats for st in row))
+        for i, s in zip(grp, ctxs):
+            q = probs[i]
+            u, _ = s.get_level(q.M)
+            errs[i] = float(np.sqrt(q.h) * np.linalg.norm(u - q.exact(q.grid(), q.T)))
+            it_q, _ = s.history(q.M)
+            flops += algorithmic_flops(q, it_q, 2)
+        for row in gstats[-1:]:
+            for i, st in zip(grp, row):
+                kernel_ms += st["device_ms"]
+                if args.precision == "mixed":
+                    L = max(8, 1 << math.ceil(math.log2(2 * probs[i].n)))
+                    flops += st["outer_iterations"] * (5.0 * L * math.log2(L) + 3.0 * L)
+        if gi == 0:
+            # history phase at the last level of the first instance (its method: fast or direct)
+            s0 = ctxs[0]
+            jh = q0.M - 1
+            s0.history_sum(jh, want=False)
+            h0 = torch.cuda.Event(enable_timing=True)
+            h1 = torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            for _ in range(3):
+                s0.history_sum(jh, want=False)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            hms = h0.elapsed_time(h1) / 3
+            hd0 = torch.cuda.Event(enable_timing=True)
+            hd1 = torch.cuda.Event(enable_timing=True)
+            hd0.record(stream)
+            s0.history_sum(jh, want=False, direct=True)
+            hd1.record(stream)
+            torch.cuda.synchronize()
+            hdms = hd0.elapsed_time(hd1)
+            hbytes = 8.0 * q0.n * jh + 16.0 * q0.n
+            peak = hbm_peak()
+            hist = {"kernel": "history phase (level M-1), direct sum", "bound": "hbm",
+                    "achieved": hbytes / (hdms / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
+                    "frac": hbytes / (hdms / 1e3) / 1e9 / peak[0], "ms": hdms,
+                    "fp64_tflops": 2.0 * q0.n * jh / (hdms / 1e3) / 1e12,
+                    "fast_history_ms": hms if fast else None, "peak_source": peak[1]}
+            # end to end through the C ABI for this group: H2D of u^0, march, D2H of u^M
+            u0s = [torch.from_numpy(s.get_level(0)[0]).pin_memory() for s in ctxs]
+            uMs = [torch.empty(probs[i].n, dtype=torch.float64).pin_memory() for i in grp]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s, a_, b_ in zip(ctxs, u0s, uMs):
+                s.reset(u0_ptr=a_.data_ptr())
+                s.solve(out_ptr=b_.data_ptr())
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            nsum = sum(probs[i].n * probs[i].M for i in grp)
+            e2e = {"value": nsum / e2e_s, "unit": "updates/s",
+                   "h2d_bytes_per_step": 8 * sum(probs[i].n for i in grp),
+                   "d2h_bytes_per_step": 8 * sum(probs[i].n for i in grp),
+                   "instances": len(grp), "note": "first memory group of instances"}
+        for s in ctxs:
+            s.close()
+        del ctxs
+    ms = ranks.max(ms_total)
+    clk.lines = samples            # clocks over every group's timed region
     co = None
     if args.co:
-        q = probs[0]
         half = W.config_history()[0]
-        half.M = q.M // 2
-        with P.Solver.from_problem(half, source="separable", precision=args.precision) as sh:
+        half.M = q0.M // 2
+        with make(half) as sh:
             uh = sh.solve()
         eh = float(np.sqrt(half.h) * np.linalg.norm(uh - half.exact(half.grid(), half.T)))
         co = {"E_M/2": eh, "E_M": errs[0], "CO_tau": math.log2(eh / errs[0])}
-    # algorithmic flops of the timed marches (level kernel roofline) and kernel time
-    flops = 0.0
-    for q, s in zip(probs, ctxs):
-        it_q, _ = s.history(q.M)
-        flops += algorithmic_flops(q, it_q, 2)
-    if args.precision == "mixed":
-        for q, st in zip(probs, stats[-1]):
-            L = max(8, 1 << math.ceil(math.log2(2 * q.n)))
-            flops += st["outer_iterations"] * (5.0 * L * math.log2(L) + 3.0 * L)
-    kernel_ms = float(sum(st["device_ms"] for st in stats[-1]))
-    launches = int(sum(st["device_launches"] for step in stats for st in step))
-    # end to end through the C ABI: H2D of u^0 and D2H of u^M per instance from pinned memory
-    import torch as _t
-    u0s = [_t.from_numpy(s.get_level(0)[0]).pin_memory() for s in ctxs]
-    uMs = [_t.empty(q.n, dtype=_t.float64).pin_memory() for q in probs]
-    _t.cuda.synchronize()
-    t0 = time.perf_counter()
-    for q, s, a, b in zip(probs, ctxs, u0s, uMs):
-        s.reset(u0_ptr=a.data_ptr())
-        s.solve(out_ptr=b.data_ptr())
-    _t.cuda.synchronize()
-    e2e_s = ranks.max(time.perf_counter() - t0)
-    for s in ctxs:
-        s.close()
     if ranks.rank != 0:
         return
-    its = [st["total_iterations"] / max(1, st["levels_advanced"]) for step in stats for st in step]
+    its = [st["total_iterations"] / max(1, st["levels_advanced"])
+           for g in stats for row in g for st in row]
     line = {"metric": "grid-point updates/s", "value": ntot * args.steps / (ms / 1e3),
             "unit": "updates/s", "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -836,17 +883,13 @@ def run_native_history(args, probs):
             "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32/ff inner / f64 refinement, f64 history",
             "data": "synthetic (manufactured solution)",
-            "config": {"workload": "tsfcde_history", "instances": len(probs_all), "n": probs[0].n,
-                       "M": probs[0].M, "alpha_beta": [[q.alpha, q.beta] for q in probs_all],
-                       "history_bytes_per_instance": 8 * probs[0].n * probs[0].M},
-            "history_roofline": {"kernel": "history phase (level M-1)", "bound": "hbm",
-                                 "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak[0],
-                                 "unit": "GB/s", "frac": hbytes / (hms / 1e3) / 1e9 / peak[0],
-                                 "ms": hms, "fp64_tflops": 2.0 * q0.n * jh / (hms / 1e3) / 1e12,
-                                 "peak_source": peak[1]},
-            "e2e": {"value": ntot / e2e_s, "unit": "updates/s",
-                    "h2d_bytes_per_step": 8 * sum(q.n for q in probs_all),
-                    "d2h_bytes_per_step": 8 * sum(q.n for q in probs_all)},
+            "config": {"workload": "tsfcde_history", "instances": len(probs_all), "n": q0.n,
+                       "M": q0.M, "alpha_beta": [[q.alpha, q.beta] for q in probs_all],
+                       "history_bytes_per_instance": 8 * q0.n * q0.M,
+                       "fast_history": fast, "memory_groups": [len(g) for g in groups],
+                       "l2": "inputs larger than L2 (history ring %.0f GB per instance)" % (8 * q0.n * q0.M / 1e9)},
+            "history_roofline": hist,
+            "e2e": e2e,
             "gpu_launches": launches,
             "roofline": roofline("level_kernel", flops, kernel_ms, args.precision),
             "cgs_iterations_mean": float(np.mean(its)), "l2_error_vs_exact_at_T": errs,
@@ -854,6 +897,29 @@ def run_native_history(args, probs):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(probs[0], args.cpu_budget)
     print(json.dumps(line))
+
+
+def profile_run(args, p):
+    """One march (or --levels levels) of the workload in the launch shape the benchmark times, and
+    nothing else: the command the committed ncu summaries under profiles/ were captured with."""
+    import paper_1603_00279_gb300 as P
+    from paper_1603_00279_gb300 import build
+    build.build()
+    if isinstance(p, list):
+        b = P.Batch(p, p[0].M, preconditioner=args.precond or "strang", precision=args.precision,
+                    maxit=args.maxit, algorithm=args.algorithm, autotune=not args.no_autotune)
+        st = b.step(p[0].M)
+        b.close()
+    else:
+        s = P.Solver.from_problem(p, source="separable", maxit=args.maxit, precision=args.precision,
+                                  autotune=not args.no_autotune,
+                                  levels_per_launch=args.levels_per_launch,
+                                  fast_history=args.fast_history == "on")
+        st = s.step(p.M)
+        s.close()
+    print(json.dumps({"profile_run": True, "levels": st["levels_advanced"],
+                      "device_ms": st["device_ms"], "launches": st["device_launches"],
+                      "cgs_iterations": st["total_iterations"]}))
 
 
 def main():
@@ -880,6 +946,12 @@ def main():
                     help="profiles/ summary holding the dominant kernel's DRAM bytes per launch")
     ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
                     help="precision workload: skip the mixed-precision march and its gap")
+    ap.add_argument("--fast-history", default="auto", choices=["auto", "on", "off"],
+                    help="history sum as a blocked FFT convolution in time (auto: on for the "
+                         "history workload only)")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="set up and march once in the timed launch shape, print a short line, "
+                         "exit (the command behind the ncu summaries in profiles/)")
     ap.add_argument("--instances", type=int, default=None,
                     help="batch workload: instance count (4096); history workload: how many of "
                          "its 16 instances to march (1)")
@@ -898,6 +970,14 @@ def main():
     if args.levels and args.workload == "history":
         for q in p:
             q.M = args.levels
+    if args.fast_history == "auto":
+        args.fast_history = "on" if args.workload == "history" else "off"
+    if args.profile_run:
+        if args.workload == "batch" and args.levels:
+            for q in p:
+                q.M = args.levels
+        profile_run(args, p if args.workload != "history" else p[0])
+        return
     if args.workload == "history":
         if args.impl == "reference":
             run_reference(args, p[0])

@@ -48,6 +48,10 @@ extern "C" {
 #define TSFCDE_E_TIMEOUT 8          /* a device-wide barrier wait ran out of its bound            */
 #define TSFCDE_E_STATE 9            /* stepping past level M, or a call in the wrong state        */
 #define TSFCDE_E_NO_DEVICE 10       /* no CUDA device / library built without a usable GPU        */
+#define TSFCDE_E_BOUNDS 11          /* libtsfcde_checked.so only (built with -DTSFCDE_CHECKED): a
+                                       device index outside its array was caught and redirected
+                                       to element 0 instead of being accessed; see
+                                       tsfcde_checked_report()                                  */
 
 /* ---- callbacks (host functions, called only during setup, on the caller's thread) ----------- */
 /* gamma(t), d_plus(t), d_minus(t) of Eq. (1.1); called at t_{j+sigma} = (j+sigma) tau. */
@@ -108,6 +112,16 @@ typedef struct tsfcde_options {
   int32_t algorithm;         /* TSFCDE_ALG_IDS (default) or TSFCDE_ALG_IDS_CONST, below        */
   int32_t test_inject;       /* testing hook, 0 normally (TSFCDE_INJECT_*, below): makes one
                                 failure path reachable from the host with valid inputs        */
+  int32_t fast_history;      /* 0 (default): the history sum of Lemma 1 summed directly at every
+                                level, O(j N) per level.  1: the same sum as a blocked
+                                convolution in time: increments in blocks of 128 levels, whose
+                                2 x 128-point FFT spectra (stored once per block, 2 x 129 x N
+                                values per block, about twice the history ring) are combined
+                                with the kernel's spectra once per block of levels; the terms of
+                                the level's own block are summed directly.  Equal to the direct
+                                sum up to rounding (FFT convolution: a relative error of a few
+                                u64 log2(256) per element).  Used when M > 128 and 2N >= 256;
+                                otherwise the direct sum runs.  Single contexts only.        */
 } tsfcde_options;
 
 /* Testing hooks (tsfcde_options.test_inject).  Valid problems cannot reach these failure paths
@@ -328,14 +342,29 @@ int tsfcde_batch_get_plan(tsfcde_batch *b, int32_t *budget, int32_t *n1_ge_n2, i
 int tsfcde_get_plan(tsfcde_ctx *ctx, int32_t *N1, int32_t *N2, int32_t *budget, double *best_us);
 
 /* Diagnostic: the history sum of Lemma 1 for level j, H_i = sum_{s<j} c^{(j)}_{j-s} (u^{s+1}_i -
- * u^s_i) (before the scaling tau^-alpha / Gamma(2-alpha)), computed by the same device phase the
- * march uses, in its own launch with the march's launch shape.  Requires 1 <= j <= current level
- * (the increments up to level j must be committed).  H_out: N host values, or NULL (device work
- * only, e.g. for timing).  Does not change the march state. */
-int tsfcde_history_sum(tsfcde_ctx *ctx, int64_t j, double *H_out);
+ * u^s_i) (before the scaling tau^-alpha / Gamma(2-alpha)), computed by the same device phases the
+ * march uses, in its own launch with the march's launch shape.  method: TSFCDE_HISTORY_CONTEXT
+ * (0) sums as the march does (the blocked FFT convolution when fast_history is on), 
+ * TSFCDE_HISTORY_DIRECT (1) always sums directly, term by term in order of s.  Requires
+ * 1 <= j <= current level (the increments up to level j must be committed).  H_out: N host
+ * values, or NULL (device work only, e.g. for timing).  Does not change the march state. */
+#define TSFCDE_HISTORY_CONTEXT 0
+#define TSFCDE_HISTORY_DIRECT 1
+int tsfcde_history_sum(tsfcde_ctx *ctx, int64_t j, int32_t method, double *H_out);
 
 /* Release everything the context holds.  NULL is allowed. */
 void tsfcde_free(tsfcde_ctx *ctx);
+
+/* TSFCDE_CHECKED builds: the first index violation the last launch of `ctx` caught (site number
+ * of the checked access and the index, truncated to 32 bits); both 0 when none was caught or in a
+ * normal build.  Reads the context's status words. */
+int tsfcde_checked_report(tsfcde_ctx *ctx, int32_t *site, int32_t *index);
+
+/* Measurement aid, no counterpart in the paper: the FP64 fused multiply-add throughput of CUDA
+ * device `device` in TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains timed
+ * with CUDA events (about 0.1 s).  The level kernels are bound by this unit; benchmarks report
+ * their algorithmic FP64 rate against it beside the peak derived from unit counts and clocks. */
+int tsfcde_measure_fp64(int32_t device, double *tflops);
 
 /* Static text for a status code. */
 const char *tsfcde_strerror(int status);

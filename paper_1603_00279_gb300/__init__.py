@@ -18,12 +18,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libtsfcde.so")
+CHECKED_LIB_PATH = os.path.join(_HERE, "_lib", "checked", "libtsfcde_checked.so")
 
 TSFCDE_OK = 0
 STATUS_NAMES = {
     0: "OK", 1: "E_INVALID_ARG", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONFINITE",
     5: "E_NOT_CONVERGED", 6: "E_BREAKDOWN", 7: "E_SINGULAR_PRECOND", 8: "E_TIMEOUT",
-    9: "E_STATE", 10: "E_NO_DEVICE",
+    9: "E_STATE", 10: "E_NO_DEVICE", 11: "E_BOUNDS",
 }
 PRECONDITIONERS = {"strang": 0, "tchan": 1, "none": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -45,7 +46,8 @@ class Options(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int32), ("outer_maxit", C.c_int32),
                 ("barrier_spin_log2", C.c_int32), ("test_skip_arrival", C.c_int32),
                 ("inner_precision", C.c_int32), ("autotune", C.c_int32),
-                ("algorithm", C.c_int32), ("test_inject", C.c_int32)]
+                ("algorithm", C.c_int32), ("test_inject", C.c_int32),
+                ("fast_history", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -109,7 +111,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_get_history.restype = C.c_int
     lib.tsfcde_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), pd]
     lib.tsfcde_get_plan.restype = C.c_int
-    lib.tsfcde_history_sum.argtypes = [vp, i64, pd]
+    lib.tsfcde_history_sum.argtypes = [vp, i64, i32, pd]
     lib.tsfcde_history_sum.restype = C.c_int
     lib.tsfcde_apply.argtypes = [vp, i32, i64, pd, pd]
     lib.tsfcde_apply.restype = C.c_int
@@ -144,9 +146,24 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.tsfcde_strerror.restype = C.c_char_p
     lib.tsfcde_version.argtypes = []
     lib.tsfcde_version.restype = C.c_char_p
+    lib.tsfcde_checked_report.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.tsfcde_checked_report.restype = C.c_int
+    lib.tsfcde_measure_fp64.argtypes = [i32, C.POINTER(dbl)]
+    lib.tsfcde_measure_fp64.restype = C.c_int
     if path is None:
         _lib = lib
     return lib
+
+
+_checked = None
+
+
+def load_checked_library() -> C.CDLL:
+    """libtsfcde_checked.so, the -DTSFCDE_CHECKED build (built by build.build(checked=True))."""
+    global _checked
+    if _checked is None:
+        _checked = load_library(CHECKED_LIB_PATH)
+    return _checked
 
 
 def _dptr(a: np.ndarray):
@@ -176,8 +193,9 @@ class Solver:
                  inner_tol: Optional[float] = None, inner_maxit: Optional[int] = None,
                  outer_maxit: Optional[int] = None, barrier_spin_log2: Optional[int] = None,
                  test_skip_arrival: bool = False, inner: str = "auto", autotune: bool = False,
-                 algorithm: str = "ids", test_inject: Optional[str] = None):
-        self.lib = load_library()
+                 algorithm: str = "ids", test_inject: Optional[str] = None,
+                 fast_history: bool = False, lib: Optional[C.CDLL] = None):
+        self.lib = lib if lib is not None else load_library()
         self.N, self.M = int(N), int(M)
         self._keep = []
 
@@ -217,6 +235,7 @@ class Solver:
         opt.autotune = 1 if autotune else 0
         opt.algorithm = ALGORITHMS[algorithm]
         opt.test_inject = INJECT[test_inject]
+        opt.fast_history = 1 if fast_history else 0
         f_cb = FIELD_FN() if f is None else field(f, True)
         if separable is not None:
             if f is not None:
@@ -307,11 +326,19 @@ class Solver:
                "tsfcde_get_plan")
         return {"N1": n1.value, "N2": n2.value, "budget": b.value, "best_us": us.value}
 
-    def history_sum(self, j: int, want: bool = True):
-        """Lemma 1 history sum of level j (unscaled), by the march's device phase."""
+    def checked_report(self):
+        """(site, index) of the first index violation caught (checked build), or (0, 0)."""
+        site, idx = C.c_int32(), C.c_int32()
+        _check(self.lib.tsfcde_checked_report(self.ctx, C.byref(site), C.byref(idx)),
+               "tsfcde_checked_report")
+        return site.value, idx.value
+
+    def history_sum(self, j: int, want: bool = True, direct: bool = False):
+        """Lemma 1 history sum of level j (unscaled), by the march's device phases (direct=True:
+        always the term-by-term sum)."""
         out = np.empty(self.N) if want else None
-        _check(self.lib.tsfcde_history_sum(self.ctx, j, _dptr(out) if want else None),
-               "tsfcde_history_sum")
+        _check(self.lib.tsfcde_history_sum(self.ctx, j, 1 if direct else 0,
+                                           _dptr(out) if want else None), "tsfcde_history_sum")
         return out
 
     def apply(self, op: str, j: int, x: np.ndarray) -> np.ndarray:
@@ -349,8 +376,8 @@ class Batch:
                  maxit: int = 2000, precision: str = "fp64", device: int = 0,
                  stream: Optional[int] = None, inner: str = "auto", algorithm: str = "ids",
                  inner_tol: Optional[float] = None, autotune: bool = False,
-                 test_inject: Optional[str] = None):
-        self.lib = load_library()
+                 test_inject: Optional[str] = None, lib: Optional[C.CDLL] = None):
+        self.lib = lib if lib is not None else load_library()
         self.M = int(M)
         self.n = [int(p.n) for p in problems]
         self._keep = []
@@ -470,6 +497,13 @@ def apply_operator_static(N: int, beta: float, sigma: float, eta: float, q: floa
     st = load_library().tsfcde_apply_operator_static(N, beta, sigma, eta, q, kappa_plus,
                                                       kappa_minus, OPS[op], x_ptr, y_ptr, stream)
     _check(st, "tsfcde_apply_operator_static")
+
+
+def measure_fp64(device: int = 0) -> float:
+    """FP64 FMA throughput of the device in TFLOP/s (tsfcde_measure_fp64)."""
+    v = C.c_double()
+    _check(load_library().tsfcde_measure_fp64(device, C.byref(v)), "tsfcde_measure_fp64")
+    return v.value
 
 
 def strerror(status: int) -> str:

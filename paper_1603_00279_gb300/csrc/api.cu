@@ -27,6 +27,7 @@ struct tsfcde_ctx {
   int64_t level = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
+  char *fh_mem = nullptr;    // fast history: block spectra, window spectra, far part
   double *ring = nullptr;
   std::vector<double> u0;
   double *omega = nullptr, *gtmp = nullptr;
@@ -46,6 +47,7 @@ struct tsfcde_ctx {
   int march_grid = 0;   // CTAs of the level-march launch (1: one-CTA team for small N)
   bool gsf_ready = false;   // Gohberg-Semencul generators built (a march passed level 1)
   size_t smem_cta = 0;      // dynamic shared memory of the one-CTA march for the final plan
+  int cta_resident = 0;     // 1: the one-CTA march keeps its working arrays in shared memory
   int march_threads = 256;  // threads per CTA of the whole-grid march
 };
 
@@ -168,6 +170,7 @@ const char *tsfcde_strerror(int status) {
     case TSFCDE_E_TIMEOUT: return "device barrier wait timed out";
     case TSFCDE_E_STATE: return "invalid state for this call";
     case TSFCDE_E_NO_DEVICE: return "no usable CUDA device";
+    case TSFCDE_E_BOUNDS: return "index out of range (checked build)";
     default: return "unknown status";
   }
 }
@@ -180,6 +183,7 @@ void tsfcde_free(tsfcde_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->ring) cudaFree(c->ring);
   if (c->arena) cudaFree(c->arena);
+  if (c->fh_mem) cudaFree(c->fh_mem);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
@@ -274,6 +278,13 @@ static int setup_impl(tsfcde_ctx *c, bool has_f) {
   A.test_skip = 0;
   A.gsf = (c->opt.algorithm == TSFCDE_ALG_IDS_CONST && M >= 2) ? 1 : 0;
   A.inject = 0;   // the device-side testing hooks are armed once setup has finished
+  // fast history: blocks of B = 128 levels, tiles of 8 lines (16 points) of 2B-point transforms
+  const bool fast_hist = c->opt.fast_history == 1 && M > 128 && A.cp.L >= 256;
+  A.fh_B = fast_hist ? 128 : 0;
+  A.fh_lgB = fast_hist ? 7 : 0;
+  A.fh_lines = fast_hist ? 8 : 0;
+  const int64_t fh_nblk = fast_hist ? (M - 1) / 128 : 0;
+  A.fh_nblk = (int)fh_nblk;
   const bool mixed = A.precision == TSFCDE_MIXED;
 
   // ---- launch shape: one CTA per SM, work split into per-CTA chunks of lines ----
@@ -423,6 +434,21 @@ static int setup_impl(tsfcde_ctx *c, bool has_f) {
   CK(cudaMalloc(&c->ring, ring_bytes));
   CK(cudaMemsetAsync(c->ring, 0, ring_bytes, c->stream));
   A.ring = c->ring;
+  if (fast_hist) {
+    // block spectra (fh_nblk x 129 x stride complex), the window spectra and the far part
+    Carver fc;
+    for (int pass = 0; pass < 2; ++pass) {
+      fc.off = 0;
+      fc.base = pass ? c->fh_mem : nullptr;
+      A.fh_E = fc.take<double2>((size_t)fh_nblk * (A.fh_B + 1) * A.ring_stride);
+      A.fh_K = fc.take<double2>((size_t)fh_nblk * (A.fh_B + 1));
+      A.fh_far = fc.take<double>((size_t)A.fh_B * A.ring_stride);
+      if (!pass) {
+        CK(cudaMalloc(&c->fh_mem, fc.off + 256));
+        CK(cudaMemsetAsync(c->fh_mem, 0, fc.off + 256, c->stream));
+      }
+    }
+  }
 
   // ---- uploads ----
   CK(cudaMemcpyAsync(c->gam, gam.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -466,6 +492,10 @@ static int setup_impl(tsfcde_ctx *c, bool has_f) {
                                (double *)A.hc, (double *)A.hl, (double *)A.lv_eta, (double *)A.lv_q,
                                (double *)A.lv_kp, (double *)A.lv_km, c->stream);
   if (st) return st;
+  if (fast_hist) {
+    st = tsf::launch_fh_kernel_spectra(A.hc, (int)M, A.fh_B, (int)fh_nblk, (double2 *)A.fh_K, c->stream);
+    if (st) return st;
+  }
   auto run_setup = [&]() -> int {
     int s2 = reset_device_flags(c);
     if (s2) return s2;
@@ -525,10 +555,16 @@ static int setup_impl(tsfcde_ctx *c, bool has_f) {
     if (st) return st;
   }
   if (c->march_grid == 1) {
+    // one-CTA march: line buffers, and the level's working arrays in shared memory when they fit
     Args B = A;
     set_caps(B, 1, c->budget);
     c->smem_cta = tsf::level_smem_bytes(B);
     if (c->smem_cta > smem_limit) return TSFCDE_E_INVALID_ARG;
+    const size_t res = c->smem_cta + tsf::resident_patch(B, nullptr);
+    if (res <= smem_limit) {
+      c->smem_cta = res;
+      c->cta_resident = 1;
+    }
   }
   c->level = 0;
   return TSFCDE_OK;
@@ -558,6 +594,7 @@ int tsfcde_setup(tsfcde_ctx **out, double a, double b, double T, int64_t N, int6
   if (o.inner_precision < 0 || o.inner_precision > 2) return TSFCDE_E_INVALID_ARG;
   if (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST) return TSFCDE_E_INVALID_ARG;
   if (o.test_inject < TSFCDE_INJECT_NONE || o.test_inject > TSFCDE_INJECT_SINGULAR) return TSFCDE_E_INVALID_ARG;
+  if (o.fast_history != 0 && o.fast_history != 1) return TSFCDE_E_INVALID_ARG;
   tsfcde_ctx *c = new tsfcde_ctx();
   c->device = o.device;
   c->opt = o;
@@ -632,6 +669,7 @@ int tsfcde_step(tsfcde_ctx *c, int64_t nsteps, tsfcde_stats *stats) {
     if (c->march_grid == 1) {
       Args B = c->A;   // one-CTA team: every pass item belongs to the single CTA
       set_caps(B, 1, c->budget);
+      B.resident = c->cta_resident;
       st = tsf::launch_levels(B, 1, c->smem_cta, c->stream, (int)s, (int)e);
     } else {
       st = tsf::launch_levels(c->A, c->grid, c->smem, c->stream, (int)s, (int)e, c->march_threads);
@@ -772,6 +810,50 @@ int tsfcde_apply(tsfcde_ctx *c, int32_t op, int64_t j, const double *x, double *
   return dst;
 }
 
+int tsfcde_measure_fp64(int32_t device, double *tflops) {
+  if (!tflops) return TSFCDE_E_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return TSFCDE_E_NO_DEVICE;
+  CK(cudaSetDevice(device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  double *out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = TSFCDE_OK;
+  const int blocks = 8 * sms, iters = 4096;
+  float ms = 0.f;
+  if (cudaMalloc(&out, sizeof(double)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = TSFCDE_E_CUDA;
+  } else {
+    rc = tsf::launch_fp64_fma(out, blocks, iters, st);                  // warm-up
+    if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = TSFCDE_E_CUDA;
+    for (int r = 0; r < 4 && !rc; ++r) rc = tsf::launch_fp64_fma(out, blocks, iters, st);
+    if (!rc && cudaEventRecord(e1, st) != cudaSuccess) rc = TSFCDE_E_CUDA;
+    if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = TSFCDE_E_CUDA;
+    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = TSFCDE_E_CUDA;
+  }
+  if (!rc) *tflops = 4.0 * blocks * 256.0 * 16.0 * iters * 2.0 / (ms / 1e3) / 1e12;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+int tsfcde_checked_report(tsfcde_ctx *c, int32_t *site, int32_t *index) {
+  if (!c) return TSFCDE_E_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  int h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, c->A.status, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (site) *site = h[2];
+  if (index) *index = h[3];
+  return TSFCDE_OK;
+}
+
 int tsfcde_get_plan(tsfcde_ctx *c, int32_t *N1, int32_t *N2, int32_t *budget, double *best_us) {
   if (!c) return TSFCDE_E_INVALID_ARG;
   if (N1) *N1 = c->A.cp.N1;
@@ -781,13 +863,18 @@ int tsfcde_get_plan(tsfcde_ctx *c, int32_t *N1, int32_t *N2, int32_t *budget, do
   return TSFCDE_OK;
 }
 
-int tsfcde_history_sum(tsfcde_ctx *c, int64_t j, double *H_out) {
-  if (!c || j < 1 || j > c->level) return TSFCDE_E_INVALID_ARG;
+int tsfcde_history_sum(tsfcde_ctx *c, int64_t j, int32_t method, double *H_out) {
+  if (!c || j < 1 || j > c->level || (method != TSFCDE_HISTORY_CONTEXT && method != TSFCDE_HISTORY_DIRECT))
+    return TSFCDE_E_INVALID_ARG;
   CK(cudaSetDevice(c->device));
   int st = reset_device_flags(c);
   if (st) return st;
-  // H is rewritten by every level before use, so it serves as the output here
-  st = tsf::launch_history(c->A, c->grid, c->smem, c->stream, (int)j);
+  // H is rewritten by every level before use, so it serves as the output here; with fast history
+  // the far part of j's block is rebuilt into the march's far buffer, which the next launch of the
+  // march rebuilds for its own block before use
+  Args A = c->A;
+  if (method == TSFCDE_HISTORY_DIRECT) A.fh_B = 0;
+  st = tsf::launch_history(A, c->grid, c->smem, c->stream, (int)j);
   if (st) return st;
   if (H_out) CK(cudaMemcpyAsync(H_out, c->A.H, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -478,6 +478,7 @@ int tsfcde_batch_setup(tsfcde_batch **out, int64_t count, const tsfcde_instance 
       (o.algorithm != TSFCDE_ALG_IDS && o.algorithm != TSFCDE_ALG_IDS_CONST))
     return TSFCDE_E_INVALID_ARG;
   if (o.test_inject != TSFCDE_INJECT_NONE && o.test_inject != TSFCDE_INJECT_NOMEM) return TSFCDE_E_INVALID_ARG;
+  if (o.fast_history != 0) return TSFCDE_E_INVALID_ARG;   // single contexts only
   size_t total = 0;
   for (int64_t i = 0; i < count; ++i) {
     const tsfcde_instance &I = inst[i];

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_setup_kernel(BatchArgs B) {
       sA = B.inst[i];
       patch_cta_scratch(sA, B.cta[blockIdx.x]);
       team().grid = 0;
+      team().abort = 0;   // the abort mirror is per instance
     }
     __syncthreads();
     const InstanceSetup &I = B.setup[i];
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_level_kernel(BatchArgs B, i
     if (threadIdx.x == 0) {
       sA = B.inst[i];
       patch_cta_scratch(sA, B.cta[blockIdx.x]);
+      team().abort = 0;   // the abort mirror is per instance
     }
     __syncthreads();
     const Smem S = smem_view(lp_max_of(sA), tw_max_of(sA));

@@ -18,7 +18,9 @@ struct Smem {
 };
 
 __device__ __forceinline__ int tw_max_of(const Args &A) {
-  return 1 << max(max(A.cp.lg1, A.cp.lg2), max(A.bp.lg1, A.bp.lg2));
+  int lt = max(max(A.cp.lg1, A.cp.lg2), max(A.bp.lg1, A.bp.lg2));
+  if (A.fh_B) lt = max(lt, A.fh_lgB + 1);
+  return 1 << lt;
 }
 
 __device__ __forceinline__ Smem smem_view(int lp_max, int tw_max) {
@@ -36,6 +38,7 @@ __device__ __forceinline__ int lp_max_of(const Args &A) {
   m = max(m, (2 * A.cap_row) << A.cp.lg2);
   m = max(m, A.cap_bcol << A.bp.lg1);
   m = max(m, A.cap_brow << A.bp.lg2);
+  if (A.fh_B) m = max(m, A.fh_lines << (A.fh_lgB + 1));
   return m;
 }
 
@@ -48,7 +51,7 @@ __device__ __forceinline__ void load_line_twiddles(const Args &A, const Smem &S,
   if (tg.tab == static_cast<const void *>(twG) && tg.dst == S.tw && tg.lg == lgP) return;
   const int P = 1 << lgP, sh = A.cp.lgL - lgP;
   T *tw = static_cast<T *>(S.tw);
-  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = twG[m << sh];
+  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = twG[TSF_CHK(m << sh, A.cp.L, 1)];
   __syncthreads();
   if (threadIdx.x == 0) {
     tg.tab = twG;
@@ -91,9 +94,9 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *
     if (INV) {
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
-        T v = Yin[(k1 << lg2) + m2];
-        if (Yin2) v = csub(v, Yin2[(k1 << lg2) + m2]);
-        a[(l << lg1) + k1] = cmulc(v, twG[(m2 * k1) << tws]);
+        T v = Yin[TSF_CHK((k1 << lg2) + m2, P1 * P2, 2)];
+        if (Yin2) v = csub(v, Yin2[TSF_CHK((k1 << lg2) + m2, P1 * P2, 3)]);
+        a[(l << lg1) + k1] = cmulc(v, twG[TSF_CHK((m2 * k1) << tws, A.cp.L, 4)]);
       }
       __syncthreads();
       a = smem_fft<+1>(a, b, lg1, cnt, tw, lg1);
@@ -102,14 +105,14 @@ __device__ __forceinline__ void col_pass(const Args &A, const Smem &S, const T *
     for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
       const int l = e % cnt, m1 = e / cnt, m2 = c0 + l;
       const int idx = (l << lg1) + m1;
-      a[idx] = body((m1 << lg2) + m2, a[idx]);
+      a[idx] = body(TSF_CHK((m1 << lg2) + m2, P1 * P2, 5), a[idx]);
     }
     __syncthreads();
     if (FWD) {
       a = smem_fft<-1>(a, b, lg1, cnt, tw, lg1);
       for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
         const int l = e % cnt, k1 = e / cnt, m2 = c0 + l;
-        Yout[(k1 << lg2) + m2] = cmul(a[(l << lg1) + k1], twG[(m2 * k1) << tws]);
+        Yout[TSF_CHK((k1 << lg2) + m2, P1 * P2, 6)] = cmul(a[(l << lg1) + k1], twG[TSF_CHK((m2 * k1) << tws, A.cp.L, 7)]);
       }
       __syncthreads();
     }
@@ -199,7 +202,7 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
       const int line = e >> lg2, k2 = e & (N2 - 1);
       const int it = i0 + (line >> 1);
       const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
-      a[e] = Yin[(row << lg2) + k2];
+      a[e] = Yin[TSF_CHK((row << lg2) + k2, N, 8)];
     }
     __syncthreads();
     a = smem_fft<-1>(a, b, lg2, nl, tw, lg2);
@@ -223,7 +226,7 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
       }
       const int k = ka + N1 * k2;
       const T Zk = ra[k2], Zp = rb[k2p];
-      const T w = twG[k];
+      const T w = twG[TSF_CHK(k, A.cp.L, 9)];
       const T Zc = cconj(Zp);
       const T E2 = cadd(Zk, Zc);
       const T O2 = mul_mi(csub(Zk, Zc));
@@ -232,8 +235,8 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
       const int sk = (ka << lg2) + k2, sp = (kb << lg2) + k2p;
       const bool self = (rb == ra) && (k2p == k2);
       if (MODE == 0) {
-        const T S0 = Sym[sk];
-        const T S1 = (k == 0) ? Sym[N] : cconj(Sym[sp]);
+        const T S0 = Sym[TSF_CHK(sk, N + 1, 10)];
+        const T S1 = (k == 0) ? Sym[N] : cconj(Sym[TSF_CHK(sp, N + 1, 11)]);
         const T Y0 = cmul(S0, X0), Y1 = cmul(S1, X1);
         const T Ep = cadd(Y0, Y1);
         const T Op = cmulc(csub(Y0, Y1), w);
@@ -245,8 +248,8 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
         const double2 v0 = make_double2((double)X0.x * sc, (double)X0.y * sc);
         const double2 v1 = make_double2((double)X1.x * sc, -(double)X1.y * sc);
         const double2 vn = make_double2((double)X1.x * sc, (double)X1.y * sc);
-        Sout[sk] = v0;
-        if (!self) Sout[sp] = v1;
+        Sout[TSF_CHK(sk, N + 1, 12)] = v0;
+        if (!self) Sout[TSF_CHK(sp, N + 1, 13)] = v1;
         if (k == 0) Sout[N] = vn;
         if (A.precision == kMixed && sym_level >= 0 && Sout == A.SP) {
           A.SP32[sk] = to_f2(v0);
@@ -275,7 +278,7 @@ __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *
         const int it = i0 + (line >> 1);
         const int row = (line & 1) ? ((N1 - it) & (N1 - 1)) : it;
         if ((line & 1) && row == it) continue;   // self-paired row stored once
-        Yout[(row << lg2) + k2] = a[e];
+        Yout[TSF_CHK((row << lg2) + k2, N, 14)] = a[e];
       }
       __syncthreads();
     }
@@ -298,17 +301,17 @@ __device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const do
   for (int r0 = lo; r0 < hi; r0 += A.cap_brow) {
     const int cnt = min(A.cap_brow, hi - r0);
     double2 *a = static_cast<double2 *>(S.a), *b = static_cast<double2 *>(S.b);
-    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = A.Y1[(r0 << lg2) + e];
+    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = A.Y1[TSF_CHK((r0 << lg2) + e, P.Nc, 15)];
     __syncthreads();
     a = smem_fft<-1>(a, b, lg2, cnt, tw, lg2);
     b = (a == static_cast<double2 *>(S.a)) ? static_cast<double2 *>(S.b) : static_cast<double2 *>(S.a);
     if (MODE == 0) {
-      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = cmul(a[e], Tab[(r0 << lg2) + e]);
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) a[e] = cmul(a[e], Tab[TSF_CHK((r0 << lg2) + e, P.Nc, 16)]);
       __syncthreads();
       a = smem_fft<+1>(a, b, lg2, cnt, tw, lg2);
-      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) A.Y2[(r0 << lg2) + e] = a[e];
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) A.Y2[TSF_CHK((r0 << lg2) + e, P.Nc, 17)] = a[e];
     } else {
-      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) Out[(r0 << lg2) + e] = cscale(a[e], scale);
+      for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) Out[TSF_CHK((r0 << lg2) + e, P.Nc, 18)] = cscale(a[e], scale);
     }
     __syncthreads();
   }
@@ -318,15 +321,17 @@ __device__ __forceinline__ void crow_pass(const Args &A, const Smem &S, const do
 // helpers on the level state
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ double source_at(const Args &A, int j, int i) {
-  if (A.f_dense) return A.f_dense[(long long)j * A.n + i];
+  if (A.f_dense) return A.f_dense[TSF_CHK((long long)j * A.n + i, (long long)A.M * A.n, 19)];
   double s = 0.0;
-  for (int r = 0; r < A.src_rank; ++r) s += A.src_t[(long long)r * A.M + j] * A.src_x[(long long)r * A.n + i];
+  for (int r = 0; r < A.src_rank; ++r)
+    s += A.src_t[TSF_CHK((long long)r * A.M + j, (long long)A.src_rank * A.M, 20)] *
+         A.src_x[TSF_CHK((long long)r * A.n + i, (long long)A.src_rank * A.n, 21)];
   return s;
 }
 
 // eigenvalue of the level-j circulant preconditioner at n-frequency m (Eq. (3.7), diagonalised)
 __device__ __forceinline__ double2 lambda_p(const Args &A, const LevelScalars &s, int m) {
-  const double2 lw = A.LamW[m], lq = A.LamQ[m];
+  const double2 lw = A.LamW[TSF_CHK(m, A.n, 22)], lq = A.LamQ[TSF_CHK(m, A.n, 23)];
   // q*lq + kp*lw + km*conj(lw)
   const double re = s.q * lq.x + (s.kp + s.km) * lw.x;
   const double im = s.q * lq.y + (s.kp - s.km) * lw.y;
@@ -413,7 +418,7 @@ static __device__ void ph_pinv_b1(const Args &A, const Smem &S, int j) {
                                    dmin = fmin(dmin, d);
                                    dmax = fmax(dmax, d);
                                    const double2 inv = make_double2(lp.x / d, -lp.y / d);
-                                   return cmul(inv, A.chirpI[m]);
+                                   return cmul(inv, A.chirpI[TSF_CHK(m, n, 24)]);
                                  });
   block_minmax(dmin, dmax, S.red);
   if (threadIdx.x == 0) {
@@ -442,7 +447,7 @@ static __device__ void ph_pinv_b3(const Args &A, const Smem &S) {
   const int n = A.n;
   col_pass<true, false, double2>(A, S, A.twL, A.bp.lg1, A.bp.lg2, 0, A.cap_bcol, A.Y2, nullptr,
                                  [&](int m, double2 z) -> double2 {
-                                   if (m < n) A.cprime[m] = cmul(z, A.chirpI[m]).x;
+                                   if (m < n) A.cprime[TSF_CHK(m, n, 25)] = cmul(z, A.chirpI[TSF_CHK(m, n, 26)]).x;
                                    return z;
                                  });
 }
@@ -456,7 +461,7 @@ static __device__ void ph_pinv_c1(const Args &A, const Smem &S) {
                                    for (int h = 0; h < 2; ++h) {
                                      const int i = 2 * m + h;
                                      // t_{-d} = c'_{n-d}
-                                     v[h] = i < n ? A.cprime[i] : (i > L - n ? A.cprime[i + n - L] : 0.0);
+                                     v[h] = i < n ? A.cprime[TSF_CHK(i, n, 27)] : (i > L - n ? A.cprime[TSF_CHK(i + n - L, n, 28)] : 0.0);
                                    }
                                    return make_double2(v[0], v[1]);
                                  });
@@ -503,6 +508,11 @@ static __device__ void ph_history(const Args &A, int j, bool commit) {
   const int npair = (A.n + 1) >> 1;
   const long long st = A.ring_stride;
   const double2 *ring2 = reinterpret_cast<const double2 *>(A.ring);
+  // fast history from the second block on: the far part (blocks before j's own) was formed by
+  // ph_far_update; here the endpoint term s = 0 and the direct terms s in [qB, j)
+  const bool fast = A.fh_B && j >= A.fh_B;
+  const int s0 = fast ? (j >> A.fh_lgB) << A.fh_lgB : 0;
+  const double2 *far2 = fast ? reinterpret_cast<const double2 *>(A.fh_far + (long long)(j - s0) * st) : nullptr;
   for (int t = team_tid(); t < npair; t += team_threads()) {
     double2 dlast = make_double2(0.0, 0.0);
     if (commit) {
@@ -513,7 +523,25 @@ static __device__ void ph_history(const Args &A, int j, bool commit) {
       reinterpret_cast<double2 *>(A.u)[t] = xv;
     }
     double hx = 0.0, hy = 0.0;
-    if (j >= 1) {
+    if (fast) {
+      const double2 fv = far2[t];
+      const double2 d0 = ring2[t];
+      const double cl = A.hl[j];
+      hx = fv.x + cl * d0.x;
+      hy = fv.y + cl * d0.y;
+      const int smax = commit ? j - 1 : j;
+      for (int s = s0; s < smax; ++s) {
+        const double2 d = ring2[TSF_CHK(s * (st >> 1) + t, (long long)A.M * (st >> 1), 29)];
+        const double c = A.hc[j - s];
+        hx += c * d.x;
+        hy += c * d.y;
+      }
+      if (commit) {   // s = j-1 >= s0 >= B from registers
+        const double c = A.hc[1];
+        hx += c * dlast.x;
+        hy += c * dlast.y;
+      }
+    } else if (j >= 1) {
       // s = 0 term: c^{(j)}_j = a_j - b_j; 1 <= s <= j-1: c^{(j)}_{j-s} = a + b - b (Lemma 1)
       const int smax = commit ? j - 1 : j;   // levels read from the ring
       int s = 0;
@@ -521,7 +549,7 @@ static __device__ void ph_history(const Args &A, int j, bool commit) {
       for (; s + kHistUnroll <= smax; s += kHistUnroll) {
         double2 d[kHistUnroll];
 #pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) d[u] = ring2[(s + u) * (st >> 1) + t];
+        for (int u = 0; u < kHistUnroll; ++u) d[u] = ring2[TSF_CHK((s + u) * (st >> 1) + t, (long long)A.M * (st >> 1), 30)];
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
           const double c = (s + u) == 0 ? A.hl[j] : A.hc[j - s - u];
@@ -530,7 +558,7 @@ static __device__ void ph_history(const Args &A, int j, bool commit) {
         }
       }
       for (; s < smax; ++s) {
-        const double2 d = ring2[s * (st >> 1) + t];
+        const double2 d = ring2[TSF_CHK(s * (st >> 1) + t, (long long)A.M * (st >> 1), 31)];
         const double c = s == 0 ? A.hl[j] : A.hc[j - s];
         hx += c * d.x; hy += c * d.y;
       }
@@ -551,6 +579,86 @@ static __device__ void ph_commit(const Args &A, int j) {
     const double2 uv = reinterpret_cast<const double2 *>(A.u)[t];
     reinterpret_cast<double2 *>(A.ring + (long long)j * A.ring_stride)[t] = make_double2(xv.x - uv.x, xv.y - uv.y);
     reinterpret_cast<double2 *>(A.u)[t] = xv;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Fast history: the sum of Lemma 1 as a blocked convolution in time.
+//   H^j = c^{(j)}_j d^0 + sum_{s=1}^{j-1} hc[j-s] d^s,   hc[m] = a_m + b_{m+1} - b_m  (Lemma 1)
+// is, for s >= 1, a causal convolution of the increments with the kernel hc.  With blocks of B
+// levels, level j = qB + r takes from the blocks p < q (increments s = pB + v, v < B, s >= 1)
+//   Far_q[r] = sum_{p<q} sum_v hc[(q-p)B + r - v] d^{pB+v}.
+// Per point and block p this is the 2B-point circular convolution of [d^{pB..pB+B-1}, 0] with the
+// kernel window w_{q-p}[t] = hc[(q-p-1)B + t] (t < 2B; hc[0] taken as 0), read at output B + r:
+// the window's other taps meet the zero half, so no wrap-around enters.  By the convolution
+// theorem
+//   Far_q[r] = IDFT_2B( sum_{p<q} DFT(w_{q-p}) . DFT([d_p, 0]) )[B + r],
+// so each block's spectrum is computed once, when the block is complete, and each later block of
+// levels costs one frequency-domain accumulation and one inverse transform per point instead of
+// q B products.  ph_history adds the endpoint term and the direct terms s in [qB, j).
+// Two points share one complex transform (real and imaginary parts), separated by the conjugate
+// symmetry of the spectra of real sequences.  Tiles of 2 fh_lines consecutive points go to the
+// team's CTAs; `transform` also computes and stores the spectrum of block q - 1.
+// ------------------------------------------------------------------------------------------------
+static __device__ void ph_far_update(const Args &A, const Smem &S, int q, bool transform) {
+  const int B = A.fh_B, lgT = A.fh_lgB + 1, T2 = 2 * B;
+  const int lines = A.fh_lines, P = 2 * lines;
+  const long long st = A.ring_stride;
+  const int ntiles = (A.n + P - 1) / P;
+  const double2 *ring2 = reinterpret_cast<const double2 *>(A.ring);
+  double2 *tw = static_cast<double2 *>(S.tw);
+  int lo, hi;
+  my_items(ntiles, lo, hi);
+  if (lo < hi) load_line_twiddles<double2>(A, S, A.twL, lgT);
+  for (int tile = lo; tile < hi; ++tile) {
+    const int i0 = tile * P;   // even; i0 + P <= ring_stride (P divides 32, the stride's unit)
+    double2 *a = static_cast<double2 *>(S.a), *b = static_cast<double2 *>(S.b);
+    if (transform) {
+      const int p = q - 1;
+      // line l: z_t = d^{pB+t}_{i0+2l} + i d^{pB+t}_{i0+2l+1} for t < B (d^0 enters as 0), 0 after
+      for (int e = threadIdx.x; e < lines * T2; e += blockDim.x) {
+        const int l = e % lines, t = e / lines;
+        const int s = p * B + t;
+        double2 z = make_double2(0.0, 0.0);
+        if (t < B && s >= 1) z = ring2[TSF_CHK((long long)s * (st >> 1) + (i0 >> 1) + l, (long long)A.M * (st >> 1), 32)];
+        a[l * T2 + t] = z;
+      }
+      __syncthreads();
+      double2 *y = smem_fft<-1>(a, b, lgT, lines, tw, lgT);
+      for (int e = threadIdx.x; e < lines * (B + 1); e += blockDim.x) {
+        const int l = e % lines, k = e / lines;
+        const double2 zk = y[l * T2 + k], zm = cconj(y[l * T2 + ((T2 - k) & (T2 - 1))]);
+        const double2 ea = cscale(cadd(zk, zm), 0.5);            // (Z_k + conj Z_{-k}) / 2
+        const double2 eb = cscale(mul_mi(csub(zk, zm)), 0.5);    // (Z_k - conj Z_{-k}) / 2i
+        double2 *E = A.fh_E + TSF_CHK((long long)(p * (B + 1) + k) * st + i0 + 2 * l,
+                                      (long long)A.fh_nblk * (B + 1) * st - 1, 33);
+        E[0] = ea;
+        E[1] = eb;
+      }
+      __syncthreads();   // the block's spectrum (global) is read below by the same CTA
+    }
+    // Y_k = sum_{p<q} K_{q-p,k} (E_p,k(a) + i E_p,k(b)), then the Hermitian extension of both
+    for (int e = threadIdx.x; e < lines * (B + 1); e += blockDim.x) {
+      const int l = e % lines, k = e / lines;
+      double2 sa = make_double2(0.0, 0.0), sb = make_double2(0.0, 0.0);
+      for (int p = 0; p < q; ++p) {
+        const double2 K = A.fh_K[TSF_CHK((long long)(q - p - 1) * (B + 1) + k, (long long)A.fh_nblk * (B + 1), 34)];
+        const double2 *E = A.fh_E + TSF_CHK((long long)(p * (B + 1) + k) * st + i0 + 2 * l,
+                                            (long long)A.fh_nblk * (B + 1) * st - 1, 35);
+        const double2 ea = E[0], eb = E[1];
+        sa = cadd(sa, cmul(K, ea));
+        sb = cadd(sb, cmul(K, eb));
+      }
+      a[l * T2 + k] = make_double2(sa.x - sb.y, sa.y + sb.x);
+      if (k > 0 && k < B) a[l * T2 + T2 - k] = make_double2(sa.x + sb.y, sb.x - sa.y);
+    }
+    __syncthreads();
+    double2 *y = smem_fft<+1>(a, b, lgT, lines, tw, lgT);   // window spectra carry 1/(2B)
+    for (int e = threadIdx.x; e < lines * B; e += blockDim.x) {
+      const int l = e % lines, r = e / lines;
+      reinterpret_cast<double2 *>(A.fh_far)[TSF_CHK(((long long)r * st + i0) / 2 + l, (long long)B * st / 2, 36)] = y[l * T2 + B + r];
+    }
+    __syncthreads();
   }
 }
 
@@ -1009,6 +1117,20 @@ static __device__ void march_body(const Args &A, const Smem &S, int j0, int j1) 
           atomicExch(A.status + 1, 1);
         }
         return;   // consistent in every CTA
+      }
+    }
+    // ---- fast history: at a block start the new block's spectrum and the block's far part; at
+    //      the first level of a launch the far part of its block ----
+    if (A.fh_B && j >= A.fh_B) {
+      const bool start = (j & (A.fh_B - 1)) == 0;
+      if (start || j == j0) {
+        if (commit) {   // the block's last increment must be in the ring before its transform
+          ph_commit(A, j - 1);
+          if (!grid_sync(A)) return;
+          commit = false;
+        }
+        ph_far_update(A, S, j >> A.fh_lgB, start);
+        if (!grid_sync(A)) return;
       }
     }
     // ---- RHS: g = B u^j - hscale * H^j + f^{j+sigma} (Eq. (3.1)) ----

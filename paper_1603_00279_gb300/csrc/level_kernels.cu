@@ -23,9 +23,69 @@ namespace tsf {
 // ------------------------------------------------------------------------------------------------
 // diagnostic: the history sum of level j alone (the march's phase, no commit)
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) history_kernel(Args A, int j) {
+__global__ void __launch_bounds__(kThreads, 1) history_kernel(Args Ap, int j) {
+  __shared__ Args A;
+  if (threadIdx.x == 0) A = Ap;
+  __syncthreads();
+  const Smem S = smem_view(lp_max_of(A), tw_max_of(A));
   grid_sync_init();
+  if (A.fh_B && j >= A.fh_B) {   // fast history: the far part of j's block from the stored spectra
+    ph_far_update(A, S, j >> A.fh_lgB, false);
+    if (!grid_sync(A)) return;
+  }
   ph_history(A, j, false);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Spectra of the fast-history kernel windows: window m = 1..nblk holds w_m[t] = hc[(m-1)B + t] for
+// t < 2B, with hc[0] taken as 0 and lags l >= M as 0 (no level uses them), and
+// K[(m-1)(B+1) + k] = DFT_2B(w_m)[k] / (2B) for k = 0..B, each by a direct sum of 2B terms.
+// ------------------------------------------------------------------------------------------------
+__global__ void fh_kernel_spectra_kernel(const double *hc, int M, int B, int nblk, double2 *K) {
+  const int T2 = 2 * B;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nblk * (B + 1); idx += gridDim.x * blockDim.x) {
+    const int m = idx / (B + 1) + 1, k = idx % (B + 1);
+    double re = 0.0, im = 0.0;
+    for (int t = 0; t < T2; ++t) {
+      const long long l = (long long)(m - 1) * B + t;
+      const double w = (l >= 1 && l < M) ? hc[l] : 0.0;
+      double sn, cs;
+      sincospi(-2.0 * (double)((k * t) % T2) / (double)T2, &sn, &cs);
+      re += w * cs;
+      im += w * sn;
+    }
+    K[idx] = make_double2(re / (double)T2, im / (double)T2);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 fused multiply-add throughput of the device (the denominator of the level kernels' ALU
+// roofline): 16 independent FMA chains per thread, enough warps per SM to keep every SM
+// sub-partition's FP64 unit busy; each FMA counts 2 flops.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double *out, int iters, double b, double c) {
+  double v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = 1e-3 * (double)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __fma_rn(v[k], b, c);
+  }
+  double sacc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sacc += v[k];
+  if (sacc == 12345.678) out[0] = sacc;   // keeps the chains live; never true for these inputs
+}
+
+int launch_fp64_fma(double *out, int blocks, int iters, cudaStream_t st) {
+  fp64_fma_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-7);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
+}
+
+int launch_fh_kernel_spectra(const double *hc, int M, int B, int nblk, double2 *K, cudaStream_t st) {
+  const int total = nblk * (B + 1);
+  fh_kernel_spectra_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, st>>>(hc, M, B, nblk, K);
+  return cudaGetLastError() == cudaSuccess ? kOK : kECuda;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -161,16 +221,7 @@ static int coop_launch(const void *fn, int grid, size_t smem, cudaStream_t st, v
   return coop_launch_n(fn, grid, kThreads, smem, st, args);
 }
 
-size_t level_smem_bytes(const Args &A) {
-  int m = A.cap_col << A.cp.lg1;
-  m = m > ((2 * A.cap_row) << A.cp.lg2) ? m : ((2 * A.cap_row) << A.cp.lg2);
-  m = m > (A.cap_bcol << A.bp.lg1) ? m : (A.cap_bcol << A.bp.lg1);
-  m = m > (A.cap_brow << A.bp.lg2) ? m : (A.cap_brow << A.bp.lg2);
-  int lt = A.cp.lg1 > A.cp.lg2 ? A.cp.lg1 : A.cp.lg2;
-  lt = lt > A.bp.lg1 ? lt : A.bp.lg1;
-  lt = lt > A.bp.lg2 ? lt : A.bp.lg2;
-  return (size_t)(2 * m + (1 << lt)) * sizeof(double2) + 4 * 32 * sizeof(double);
-}
+size_t level_smem_bytes(const Args &A) { return smem_lines_bytes(A); }
 
 const void *level_kernel_ptr() { return (const void *)level_kernel<kThreads>; }
 const void *history_kernel_ptr() { return (const void *)history_kernel; }

@@ -28,7 +28,8 @@ constexpr long long kSpinLimit = 1ll << 23;   // default bound on a barrier wait
 
 // status codes (mirror include/tsfcde.h)
 constexpr int kOK = 0, kEInvalid = 1, kENoMem = 2, kECuda = 3, kENonFinite = 4,
-              kENotConverged = 5, kEBreakdown = 6, kESingular = 7, kETimeout = 8, kEState = 9;
+              kENotConverged = 5, kEBreakdown = 6, kESingular = 7, kETimeout = 8, kEState = 9,
+              kEBounds = 11;
 constexpr int kFP64 = 0, kMixed = 1;
 
 struct ConvPlan {  // real length L, complex length N = L/2 = N1 * N2
@@ -94,6 +95,16 @@ struct Args {
   long long spin_limit;   // polls before a barrier wait gives up
   int test_skip;          // testing hook: CTA 0 skips its first barrier arrival
   int inject;             // testing hook (tsfcde_options.test_inject): 2 breakdown, 3 singular P
+  int resident;           // one-CTA march: the per-level working arrays live in shared memory
+  // fast history (blocked convolution in time by 2B-point FFTs; fh_B = 0: the direct sum)
+  int fh_B, fh_lgB;       // block length B = 2^fh_lgB in levels
+  int fh_lines;           // complex FFT lines of length 2B per shared-memory tile (2 points each)
+  int fh_nblk;            // increment blocks whose spectra are kept
+  double2 *fh_E;          // spectra of the increment blocks: block p, frequency k <= B, point i at
+                          // (p (B+1) + k) ring_stride + i
+  const double2 *fh_K;    // spectra of the kernel windows, scaled 1/(2B): window m >= 1 at
+                          // (m-1)(B+1) + k
+  double *fh_far;         // far part of the history of the current block's levels: B x ring_stride
   // float-float inner solve (mixed mode, levels where FP32 cannot resolve the operator)
   const int *lv_inner;    // per level: 0 FP32 inner solve, 1 float-float inner solve
   const double *lv_floor; // per level: FP64 residual accepted once refinement stagnates below it
@@ -389,27 +400,47 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 
+// The team of CTAs that works on one instance: the whole grid (one instance per launch) or a
+// single CTA (batched instances, one per CTA at a time; small single instances).  Kept in shared
+// memory, set at kernel start; every work split, reduction and barrier of the level solve goes
+// through it.  `abort` mirrors the instance's abort flag for a one-CTA team, so that its barriers
+// need no global-memory read.
+struct TeamInfo {
+  int idx, cnt, grid, abort;
+};
+__device__ __forceinline__ TeamInfo &team() {
+  __shared__ TeamInfo t;
+  return t;
+}
+
+// Index checks of the TSFCDE_CHECKED build: an index outside [0, n) is recorded (status word 0
+// = TSFCDE_E_BOUNDS unless an error was already set, word 2 = the first failing site, word 3 =
+// its index) and replaced by 0, so the access stays inside the array and nothing traps.  In
+// the normal build TSF_CHK(i, n, site) is just i.
+#ifdef TSFCDE_CHECKED
+static __device__ __noinline__ long long chk_fail(const Args &A, long long i, int site) {
+  if (atomicCAS(A.status + 2, 0, site) == 0) atomicExch(A.status + 3, (int)i);
+  atomicCAS(A.status, 0, kEBounds);
+  return 0;
+}
+#define TSF_CHK(i, n, site) \
+  (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n)) ? (long long)(i) : ::tsf::chk_fail(A, (long long)(i), (site)))
+#else
+#define TSF_CHK(i, n, site) (i)
+#endif
+
 // Sets a fatal status (first one wins) and raises the abort flag.
 __device__ __forceinline__ void raise_fatal(const Args &A, int code) {
   atomicCAS(A.status, 0, code);
   atomicExch(A.status + 1, 1);
   __threadfence();
+  *(volatile int *)&team().abort = 1;
 }
 
 // Barrier words: [0, 2) the 64-bit arrival counter; the rest is reserved.
 constexpr int kMaxGrid = 1024;
 constexpr int kBarWords = 32 + kMaxGrid;
 
-// The team of CTAs that works on one instance: the whole grid (one instance per launch) or a
-// single CTA (batched instances, one per CTA at a time).  Kept in shared memory, set at kernel
-// start; every work split, reduction and barrier of the level solve goes through it.
-struct TeamInfo {
-  int idx, cnt, grid;
-};
-__device__ __forceinline__ TeamInfo &team() {
-  __shared__ TeamInfo t;
-  return t;
-}
 
 // What the shared-memory line-twiddle table holds (source table, destination, line length), so
 // that a pass whose line twiddles are already there does not reload them.  Reset at kernel start.
@@ -435,6 +466,7 @@ __device__ __forceinline__ void grid_sync_init() {
     team().idx = blockIdx.x;
     team().cnt = gridDim.x;
     team().grid = 1;
+    team().abort = 0;
     tw_tag().tab = nullptr;
   }
   __syncthreads();
@@ -446,6 +478,7 @@ __device__ __forceinline__ void cta_team_init() {
     team().idx = 0;
     team().cnt = 1;
     team().grid = 0;
+    team().abort = 0;
     tw_tag().tab = nullptr;
   }
   __syncthreads();
@@ -470,7 +503,7 @@ __device__ __forceinline__ bool grid_sync(const Args &A) {
   __shared__ int s_go;
   __syncthreads();
   if (!team().grid) {   // one-CTA team: a block barrier orders the CTA's global writes
-    if (threadIdx.x == 0) s_go = ld_volatile_i32(A.status + 1) == 0;
+    if (threadIdx.x == 0) s_go = *(volatile int *)&team().abort == 0;
     __syncthreads();
     return s_go != 0;
   }
@@ -581,6 +614,90 @@ inline size_t raise_smem_limit(const void *fn, const cudaDeviceProp &prop) {
   return dyn;
 }
 
+// Bytes of the per-CTA shared-memory line buffers, line twiddles and reduction scratch of a plan
+// (the layout smem_view uses): two buffers of the largest chunk, the longest line's twiddles and
+// 4 x 32 doubles.
+__host__ __device__ inline size_t smem_lines_bytes(const Args &A) {
+  int m = A.cap_col << A.cp.lg1;
+  m = m > ((2 * A.cap_row) << A.cp.lg2) ? m : ((2 * A.cap_row) << A.cp.lg2);
+  m = m > (A.cap_bcol << A.bp.lg1) ? m : (A.cap_bcol << A.bp.lg1);
+  m = m > (A.cap_brow << A.bp.lg2) ? m : (A.cap_brow << A.bp.lg2);
+  int lt = A.cp.lg1 > A.cp.lg2 ? A.cp.lg1 : A.cp.lg2;
+  lt = lt > A.bp.lg1 ? lt : A.bp.lg1;
+  lt = lt > A.bp.lg2 ? lt : A.bp.lg2;
+  if (A.fh_B) {   // fast-history tiles: fh_lines lines of 2B points
+    m = m > (A.fh_lines << (A.fh_lgB + 1)) ? m : (A.fh_lines << (A.fh_lgB + 1));
+    lt = lt > A.fh_lgB + 1 ? lt : A.fh_lgB + 1;
+  }
+  return (size_t)(2 * m + (1 << lt)) * 16 + 4 * 32 * sizeof(double);
+}
+
+// The working arrays of one level solve that a one-CTA march keeps in shared memory after the
+// line buffers: Krylov vectors and FFT work arrays of every precision in use, the level spectra,
+// P^{-1}'s circulant column and the reduction partials.  Tables, the level state u, the history
+// ring, the Gohberg-Semencul generators and per-level outputs stay in global memory (they outlive
+// a launch).  Returns the bytes; with `base` non-null, points A's fields into [base, base+bytes).
+struct ResCarve {
+  size_t off;
+  char *base;
+  template <typename T>
+  __host__ __device__ T *take(size_t count) {
+    off = (off + 15) & ~size_t(15);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+__host__ __device__ inline size_t resident_patch(Args &A, char *base) {
+  ResCarve c{0, base};
+  const size_t L = (size_t)A.cp.L, N = (size_t)A.cp.N, n = (size_t)A.n;
+  A.x = c.take<double>(L);
+  A.r = c.take<double>(L);
+  A.rt = c.take<double>(L);
+  A.p = c.take<double>(L);
+  A.q = c.take<double>(L);
+  A.uu = c.take<double>(L);
+  A.vh = c.take<double>(L);
+  A.H = c.take<double>(L);
+  A.xb = c.take<double>(L);
+  A.Y1 = c.take<double2>(L);
+  A.Y2 = c.take<double2>(L);
+  A.SA = c.take<double2>(N + 1);
+  A.SB = c.take<double2>(N + 1);
+  A.SP = c.take<double2>(N + 1);
+  A.cprime = c.take<double>(n);
+  A.partials = c.take<double>(8);
+  if (A.gsf) A.Y3 = c.take<double2>(N);
+  if (A.precision == kMixed) {
+    A.g = c.take<double>(L);
+    A.x32 = c.take<float>(L);
+    A.r32 = c.take<float>(L);
+    A.rt32 = c.take<float>(L);
+    A.p32 = c.take<float>(L);
+    A.q32 = c.take<float>(L);
+    A.uu32 = c.take<float>(L);
+    A.vh32 = c.take<float>(L);
+    A.x32b = c.take<float>(L);
+    A.SA32 = c.take<float2>(N + 1);
+    A.SP32 = c.take<float2>(N + 1);
+    A.Y1f = c.take<float2>(N);
+    A.Y2f = c.take<float2>(N);
+    A.xff = c.take<ff>(L);
+    A.rff = c.take<ff>(L);
+    A.rtff = c.take<ff>(L);
+    A.pff = c.take<ff>(L);
+    A.qff = c.take<ff>(L);
+    A.uuff = c.take<ff>(L);
+    A.vhff = c.take<ff>(L);
+    A.xffb = c.take<ff>(L);
+    A.SAff = c.take<ffc>(N + 1);
+    A.SPff = c.take<ffc>(N + 1);
+    A.Y1ff = c.take<ffc>(N);
+    A.Y2ff = c.take<ffc>(N);
+  }
+  return (c.off + 15) & ~size_t(15);
+}
+
 // Host-side entry points implemented in level_kernels.cu.
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1,
                   int threads = kThreads);
@@ -601,6 +718,8 @@ const void *level_kernel_cta_ptr();
 const void *level_kernel_wide_ptr();
 const void *history_kernel_ptr();
 int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j);
+int launch_fh_kernel_spectra(const double *hc, int M, int B, int nblk, double2 *K, cudaStream_t st);
+int launch_fp64_fma(double *out, int blocks, int iters, cudaStream_t st);
 int launch_level_rebuild(const double *u0, const double *uc, const double *ring, long long stride, int n,
                          int j, int c, double *out, cudaStream_t st);
 const void *batch_level_kernel_ptr();

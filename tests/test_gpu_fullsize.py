@@ -57,8 +57,8 @@ def _allowed_residual(prob, j, precision, tol=1e-12):
     return max(tol, 64.0 * U64 * nA / abs(e))
 
 
-def _check_levels(prob, levels, resid, seed=0, label="", precision="fp64"):
-    """Sampled rows of levels 0..len(levels)-2 against the derived bound; returns the largest
+def _check_levels(prob, levels, resid, seed=0, label="", precision="fp64", first=0):
+    """Sampled rows of levels first..len(levels)-2 against the derived bound; returns the largest
     observed |r_i| / bound_i."""
     n = prob.n
     L = max(8, 1 << math.ceil(math.log2(2 * n)))
@@ -67,7 +67,7 @@ def _check_levels(prob, levels, resid, seed=0, label="", precision="fp64"):
     x = prob.grid()
     sigma = 1.0 - prob.alpha / 2.0
     worst = 0.0
-    for j in range(len(levels) - 1):
+    for j in range(first, len(levels) - 1):
         g, Au = O.level_equation_rows(prob, j, rows, levels[:j + 1], levels[j + 1])
         nA, nB = _row_sum_bound(prob, j)
         H = np.zeros(n)
