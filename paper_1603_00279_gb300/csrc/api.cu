@@ -369,13 +369,6 @@ static int setup_impl(tsfcde_ctx *c, bool has_f) {
     c->dp = cv.take<double>(M);
     c->dm = cv.take<double>(M);
     A.partials = cv.take<double>((size_t)2 * c->grid * 4);
-    if (c->grid % 2 == 0 && c->grid >= 2) {
-      // single-row row passes of the whole-grid march: exchange buffers and per-row flags for
-      // every split the autotuner may pick (N1 <= 2^(lgN/2 + 1))
-      A.xch = cv.take<double2>((size_t)2 * N);
-      A.xflag_rows = 1 << (A.cp.lgN / 2 + 2);
-      A.xflag = cv.take<unsigned long long>((size_t)A.xflag_rows);
-    }
     A.bar = cv.take<unsigned>(tsf::kBarWords);
     A.status = cv.take<int>(4);
     A.iters = cv.take<int>(M);

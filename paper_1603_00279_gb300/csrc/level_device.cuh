@@ -181,143 +181,9 @@ __device__ __forceinline__ void store_ab(const Args &A, const LevelScalars &s, i
   }
 }
 
-// ------------------------------------------------------------------------------------------------
-// Row pass of a whole-grid team with single-row items (MODE 0 only).  Rows are numbered
-// u = 0 -> row 0, u = 1 -> row N1/2 (both pair with themselves), u = 2k -> row k,
-// u = 2k+1 -> row N1-k; CTA c takes u = c, c + G, c + 2G, ... (G even), so rows k and N1-k are
-// handled by CTAs c and c^1 in the same round.  Each CTA forward-transforms its rows, publishes
-// them to an exchange buffer and raises the row's flag to this pass's epoch (release); it then
-// waits (bounded) for its partner rows' flags (acquire) and merges its own row with the
-// partner's values read from the buffer: for row ka the merged value at k2 is Ep + i Op of the
-// row-pair pass (the partner computes its row from its own side, which gives the pair pass's
-// conj(Ep - i Op) for it).  1026 rows spread over 152 CTAs as 6.75 each, where 513 row pairs
-// gave at most 4 against 3.4 on average.  Two exchange buffers alternate with the pass count, so
-// the two row passes a phase may run back to back never overwrite rows a partner still reads.
-// ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ int split_row(int u, int N1) {
-  if (u < 2) return u == 0 ? 0 : N1 / 2;
-  const int k = u >> 1;
-  return (u & 1) ? N1 - k : k;
-}
-
-template <typename T>
-__device__ __forceinline__ void row_pass_split(const Args &A, const Smem &S, const T *twG, const T *Yin,
-                                               T *Yout, const T *Sym) {
-  const ConvPlan &P = A.cp;
-  const int N1 = P.N1, N2 = P.N2, lg2 = P.lg2, N = P.N;
-  const int G = team().cnt, c = team().idx;
-  T *tw = static_cast<T *>(S.tw);
-  const int rounds = (N1 - c + G - 1) / G;                  // units c + rG < N1
-  const int cap = max(1, min(2 * A.cap_row, (int)(lp_max_of(A) >> lg2)));
-  __shared__ unsigned s_pass;
-  if (threadIdx.x == 0) s_pass = ++row_pass_count();
-  __syncthreads();
-  const unsigned pass = s_pass;
-  const unsigned long long epoch = (A.launch_seq << 32) | (unsigned long long)pass;
-  T *X = reinterpret_cast<T *>(A.xch) + (size_t)(pass & 1u) * N;
-  if (rounds > 0) load_line_twiddles<T>(A, S, twG, lg2);
-  for (int r0 = 0; r0 < rounds; r0 += cap) {
-    const int cnt = min(cap, rounds - r0);
-    T *a = static_cast<T *>(S.a), *b = static_cast<T *>(S.b);
-    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
-      const int l = e >> lg2, k2 = e & (N2 - 1);
-      const int row = split_row(c + (r0 + l) * G, N1);
-      a[e] = Yin[TSF_CHK((row << lg2) + k2, N, 37)];
-    }
-    __syncthreads();
-    a = smem_fft<-1>(a, b, lg2, cnt, tw, lg2);
-    // publish the rows that have a partner (u >= 2)
-    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
-      const int l = e >> lg2, k2 = e & (N2 - 1);
-      const int u = c + (r0 + l) * G;
-      if (u >= 2) X[TSF_CHK((split_row(u, N1) << lg2) + k2, N, 38)] = a[e];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      for (int l = 0; l < cnt; ++l) {
-        const int u = c + (r0 + l) * G;
-        if (u >= 2) {
-          unsigned long long *f = A.xflag + TSF_CHK(split_row(u, N1), A.xflag_rows, 39);
-          asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(epoch) : "memory");
-        }
-      }
-      // wait for the partner rows (bounded; gives up on the abort flag or the spin limit)
-      for (int l = 0; l < cnt; ++l) {
-        const int u = c + (r0 + l) * G;
-        if (u < 2) continue;
-        const unsigned long long *f = A.xflag + TSF_CHK(split_row(u ^ 1, N1), A.xflag_rows, 40);
-        long long spins = 0;
-        while (ld_acquire_u64(f) != epoch) {
-          if (++spins > A.spin_limit) {
-            raise_fatal(A, kETimeout);
-            break;
-          }
-          if ((spins & 255) == 0 && ld_volatile_i32(A.status + 1)) break;
-        }
-      }
-      __threadfence();
-    }
-    __syncthreads();
-    // merge each own row with its partner's values
-    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
-      const int l = e >> lg2, k2 = e & (N2 - 1);
-      const int u = c + (r0 + l) * G;
-      const int ka = split_row(u, N1), kb = (N1 - ka) & (N1 - 1);
-      T *ra = a + (l << lg2);
-      int k2p;
-      bool self = false;
-      T Zp;
-      if (u >= 2) {
-        k2p = N2 - 1 - k2;
-        Zp = X[TSF_CHK((kb << lg2) + k2p, N, 41)];
-      } else if (ka == 0) {   // row 0 pairs k2 with N2 - k2 inside itself
-        if (k2 > N2 / 2) continue;
-        k2p = (N2 - k2) & (N2 - 1);
-        Zp = ra[k2p];
-        self = k2p == k2;
-      } else {                // row N1/2 pairs k2 with N2-1-k2 inside itself
-        if (k2 >= N2 / 2) continue;
-        k2p = N2 - 1 - k2;
-        Zp = ra[k2p];
-      }
-      const int k = ka + N1 * k2;
-      const T Zk = ra[k2];
-      const T w = twG[TSF_CHK(k, A.cp.L, 42)];
-      const T Zc = cconj(Zp);
-      const T E2 = cadd(Zk, Zc);
-      const T O2 = mul_mi(csub(Zk, Zc));
-      const T t2 = cmul(w, O2);
-      const T X0 = cadd(E2, t2), X1 = csub(E2, t2);
-      const int sk = (ka << lg2) + k2, sp = (kb << lg2) + k2p;
-      const T S0 = Sym[TSF_CHK(sk, N + 1, 43)];
-      const T S1 = (k == 0) ? Sym[N] : cconj(Sym[TSF_CHK(sp, N + 1, 44)]);
-      const T Y0 = cmul(S0, X0), Y1 = cmul(S1, X1);
-      const T Ep = cadd(Y0, Y1);
-      const T Op = cmulc(csub(Y0, Y1), w);
-      const T iOp = mul_i(Op);
-      // a self-paired row's partner value lives in the same line: written by this thread only
-      ra[k2] = cadd(Ep, iOp);
-      if (u < 2 && !self) ra[k2p] = cconj(csub(Ep, iOp));
-    }
-    __syncthreads();
-    a = smem_fft<+1>(a, b, lg2, cnt, tw, lg2);
-    for (int e = threadIdx.x; e < cnt * N2; e += blockDim.x) {
-      const int l = e >> lg2, k2 = e & (N2 - 1);
-      const int row = split_row(c + (r0 + l) * G, N1);
-      Yout[TSF_CHK((row << lg2) + k2, N, 45)] = a[e];
-    }
-    __syncthreads();
-  }
-}
-
 template <int MODE, typename T>
 __device__ __forceinline__ void row_pass(const Args &A, const Smem &S, const T *twG, const T *Yin, T *Yout,
                                          const T *Sym, double2 *Sout, double scale, int sym_level) {
-  if (MODE == 0 && A.xch && team().grid && (team().cnt & 1) == 0) {
-    row_pass_split<T>(A, S, twG, Yin, Yout, Sym);
-    return;
-  }
   const ConvPlan &P = A.cp;
   const int N1 = P.N1, N2 = P.N2, lg2 = P.lg2, N = P.N;
   T *tw = static_cast<T *>(S.tw);

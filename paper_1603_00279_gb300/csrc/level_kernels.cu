@@ -17,7 +17,6 @@
 #include "level_device.cuh"
 
 #include <algorithm>
-#include <atomic>
 #include <cstring>
 
 namespace tsf {
@@ -235,18 +234,10 @@ int launch_history(const Args &A, int grid, size_t smem, cudaStream_t st, int j)
 const void *apply_kernel_ptr() { return (const void *)apply_kernel; }
 const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
 
-// A number no earlier launch of this process used: the epoch of the single-row row passes'
-// exchange flags, which therefore never need clearing.
-unsigned long long next_launch_seq() {
-  static std::atomic<unsigned long long> seq{1};
-  return seq.fetch_add(1);
-}
-
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1, int threads) {
   if (grid == 1) return launch_levels_cta(A, smem, st, j0, j1);   // one-CTA team (level_wide.cu)
   if (threads == kWideThreads) return launch_levels_wide(A, grid, smem, st, j0, j1);
   Args a = A;
-  a.launch_seq = next_launch_seq();
   void *args[] = {&a, &j0, &j1};
   return coop_launch_n((const void *)level_kernel<kThreads>, grid, kThreads, smem, st, args);
 }
@@ -254,7 +245,6 @@ int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0,
 int launch_apply(const Args &A, int grid, size_t smem, cudaStream_t st, int op, int j,
                  const double *xin, double *yout) {
   Args a = A;
-  a.launch_seq = next_launch_seq();
   void *args[] = {&a, &op, &j, &xin, &yout};
   return coop_launch((const void *)apply_kernel, grid, smem, st, args);
 }

@@ -34,7 +34,6 @@ const void *level_kernel_cta_ptr() { return (const void *)level_kernel_cta; }
 
 int launch_levels_wide(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1) {
   Args a = A;
-  a.launch_seq = next_launch_seq();
   void *args[] = {&a, &j0, &j1};
   return coop_launch_n((const void *)level_kernel<kWideThreads>, grid, kWideThreads, smem, st, args);
 }

@@ -96,11 +96,6 @@ struct Args {
   int test_skip;          // testing hook: CTA 0 skips its first barrier arrival
   int inject;             // testing hook (tsfcde_options.test_inject): 2 breakdown, 3 singular P
   int resident;           // one-CTA march: the per-level working arrays live in shared memory
-  // single-row items of the whole-grid row pass: partner CTAs swap forward-transformed rows
-  double2 *xch;           // two exchange buffers of N complex (16 bytes per element), or null
-  unsigned long long *xflag;   // per row: epoch of its latest publication
-  int xflag_rows;         // rows the flag array covers
-  unsigned long long launch_seq;   // distinct for every launch of a context (host-set)
   // fast history (blocked convolution in time by 2B-point FFTs; fh_B = 0: the direct sum)
   int fh_B, fh_lgB;       // block length B = 2^fh_lgB in levels
   int fh_lines;           // complex FFT lines of length 2B per shared-memory tile (2 points each)
@@ -459,12 +454,6 @@ __device__ __forceinline__ TwTag &tw_tag() {
   return t;
 }
 
-// Per-CTA count of single-row row passes run in this launch (the same in every CTA).
-__device__ __forceinline__ unsigned &row_pass_count() {
-  __shared__ unsigned k;
-  return k;
-}
-
 // Per-CTA count of grid barriers passed in this launch.
 __device__ __forceinline__ unsigned long long &bar_count() {
   __shared__ unsigned long long k;
@@ -479,7 +468,6 @@ __device__ __forceinline__ void grid_sync_init() {
     team().grid = 1;
     team().abort = 0;
     tw_tag().tab = nullptr;
-    row_pass_count() = 0u;
   }
   __syncthreads();
 }
@@ -711,7 +699,6 @@ __host__ __device__ inline size_t resident_patch(Args &A, char *base) {
 }
 
 // Host-side entry points implemented in level_kernels.cu.
-unsigned long long next_launch_seq();
 int launch_levels(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1,
                   int threads = kThreads);
 int launch_levels_wide(const Args &A, int grid, size_t smem, cudaStream_t st, int j0, int j1);
