@@ -383,9 +383,10 @@ def captured_traffic(name: str):
         return None, f"no capture ({name})"
     kv = {}
     for l in lines:
-        if ":" in l and l.strip().startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
+        l = l.strip().lstrip("-* `")
+        if ":" in l and l.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
             k, v = l.split(":", 1)
-            kv[k.strip().lstrip("-* `")] = v.strip().strip("`")
+            kv[k.strip()] = v.strip().strip("`")
     try:
         traffic = float(kv["traffic_bytes_per_launch"])
         sha = kv["kernel_sources_sha256"]
