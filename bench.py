@@ -160,6 +160,21 @@ def _alg_flops(n, M, preconditioner, iters, newsym_levels):
     return conv * convs + sym * newsym_levels + hist + vec
 
 
+def _fast_history_flops(n, M, B=128):
+    """FP64 flops of the history sum as the fast history computes it (blocked FFT convolution in
+    time, blocks of B levels), per march: per block start q >= 1 one 2B-point complex FFT per two
+    points for the new block and one inverse per two points (5 B log2(2B) flops per point each),
+    and q (B+1) complex multiply-adds (8 flops) per point; per level the endpoint term, the far
+    part and the direct terms of its own block (2 flops each)."""
+    lg = math.log2(2 * B)
+    f = 0.0
+    for q in range(1, (M - 1) // B + 1):
+        f += 2 * 5.0 * B * lg + 8.0 * q * (B + 1)
+    for j in range(1, M):
+        f += 2.0 * (j % B) + 3.0 if j >= B else 2.0 * j
+    return f * n
+
+
 def _alg_flops_const(n, M, preconditioner, iters, applications):
     """Algorithm "... with constant coefficients": the CGS iterations of level 0 and of the two
     generator solves, one right-hand-side product per level, and per application of A^{-1}
@@ -821,6 +836,8 @@ def run_native_history(args, probs):
             errs[i] = float(np.sqrt(q.h) * np.linalg.norm(u - q.exact(q.grid(), q.T)))
             it_q, _ = s.history(q.M)
             flops += algorithmic_flops(q, it_q, 2)
+            if fast:   # the history as the fast history computes it, not as the direct sum
+                flops += _fast_history_flops(q.n, q.M) - 2.0 * q.n * (q.M * (q.M - 1) / 2.0)
         for row in gstats[-1:]:
             for i, st in zip(grp, row):
                 kernel_ms += st["device_ms"]
@@ -897,6 +914,8 @@ def run_native_history(args, probs):
                        "M": q0.M, "alpha_beta": [[q.alpha, q.beta] for q in probs_all],
                        "history_bytes_per_instance": 8 * q0.n * q0.M,
                        "fast_history": fast, "memory_groups": [len(g) for g in groups],
+                       "history_flops": ("blocked FFT convolution in time, as computed" if fast
+                                         else "direct sum (2 j n per level)"),
                        "l2": "inputs larger than L2 (history ring %.0f GB per instance)" % (8 * q0.n * q0.M / 1e9)},
             "history_roofline": hist,
             "e2e": e2e,

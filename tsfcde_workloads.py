@@ -22,7 +22,7 @@ Workloads (sizes are interior unknowns n, the paper's N-1):
   * `config_large`   n=65535, M=1024, alpha=0.3, beta=1.9, same coefficient forms and solution.
   * `config_mixed`   n=2^20-1, M=512, alpha=0.8, beta=1.5, gamma=1, d+-=(1 +- t/2)/2.
   * `config_batch`   seeded instances with log-uniform n in [255, 16383] and constant coefficients.
-  * `config_history` 16 instances of n=2^18-1, M=8192.
+  * `config_history` 16 instances of n=2^18-1, M=8192 (8 (alpha, beta) combinations, each twice).
   * `example1`/`example2`: the paper's Examples 1 and 2 (Section 4), u=(t^(2+alpha)+1)X.
 """
 from __future__ import annotations
@@ -174,9 +174,10 @@ def config_mixed(n=(1 << 20) - 1, M=512, alpha=0.8, beta=1.5, preconditioner="st
 
 
 def config_history(n=(1 << 18) - 1, M=8192, preconditioner="strang"):
-    """History-dominated workload: 16 instances, alpha x beta grid with the first 2 repeated."""
+    """History-dominated workload: 16 instances, the 8 combinations of alpha in
+    {0.2, 0.5, 0.9, 0.99} and beta in {1.2, 1.8}, each twice (16 instances from 8 combinations)."""
     combos = [(a, b) for a in (0.2, 0.5, 0.9, 0.99) for b in (1.2, 1.8)]
-    combos = combos + combos[:2]
+    combos = combos + combos
     return [_make(n, M, a, b, lambda t: 0.5, lambda t: 1.0 + t, lambda t: 1.0 - 0.5 * t,
                   manufactured_t2, preconditioner=preconditioner, name=f"history{i}")
             for i, (a, b) in enumerate(combos)]
