@@ -893,12 +893,21 @@ def run_native_history(args, probs):
     clk.lines = samples            # clocks over every group's timed region
     co = None
     if args.co:
-        half = W.config_history()[0]
-        half.M = q0.M // 2
-        with make(half) as sh:
-            uh = sh.solve()
-        eh = float(np.sqrt(half.h) * np.linalg.norm(uh - half.exact(half.grid(), half.T)))
-        co = {"E_M/2": eh, "E_M": errs[0], "CO_tau": math.log2(eh / errs[0])}
+        # the order of the scheme, from FP64 marches (tol 1e-12): the mixed march's FP64 residual
+        # floor 64 u64 kappa_eff is within a factor of a few of the error at T on this workload
+        def err_fp64(q):
+            with P.Solver.from_problem(q, source="separable", stream=stream.cuda_stream,
+                                       precision="fp64", maxit=args.maxit, fast_history=fast,
+                                       autotune=not args.no_autotune) as sf:
+                uq = sf.solve()
+            return float(np.sqrt(q.h) * np.linalg.norm(uq - q.exact(q.grid(), q.T)))
+        half, quarter = W.config_history()[0], W.config_history()[0]
+        half.M, quarter.M = q0.M // 2, q0.M // 4
+        e_full, e_half, e_q = err_fp64(W.config_history()[0]), err_fp64(half), err_fp64(quarter)
+        co = {"E_M/4": e_q, "E_M/2": e_half, "E_M": e_full, "CO_tau": math.log2(e_half / e_full),
+              "CO_tau_M4_M2": math.log2(e_q / e_half), "precision": "fp64",
+              "note": "at M the scheme's error is a few times the solves' accumulated error at "
+                      "tol 1e-12; (M/4, M/2) pins the order"}
     if ranks.rank != 0:
         return
     its = [st["total_iterations"] / max(1, st["levels_advanced"])
