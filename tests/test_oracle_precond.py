@@ -124,3 +124,31 @@ def test_preconditioned_spectrum_clusters_at_one(j):
     assert 6 <= outliers <= 10, outliers
     assert np.abs(lam).min() > 0.5
     assert lamA.max() / lamA.min() > 100.0
+
+
+def test_tchan_misses_the_smallest_eigenvalues_on_the_large_workload():
+    """The large workload's coefficients (alpha = 0.3, beta = 1.9, tau = 1/1024) at n = 1023.
+    T. Chan's circulant averages each diagonal with its wrapped partner, so its zero-frequency
+    eigenvalue is the mean row sum (1/n) 1^T P 1, which the boundary rows of the fractional
+    operator make large: min|Lambda_P| is far above eta, while Strang's stays near eta.  On the
+    smoothest mode sin(pi x), where A is near its smallest eigenvalue, P^{-1} A is then far below
+    1 for T. Chan and of order 1 for Strang, and CGS needs several times Strang's iterations.
+    (At n = 65535 the same gap grows to 6.9e4 against eta = 7.86.)"""
+    p = W.config_large(n=1023, M=1024)
+    A, B = O.level_matrices(p, 0)
+    eta = O.eta(p.alpha, p.tau, 0)
+    sigma = 1 - p.alpha / 2
+    g = B @ p.phi(p.grid()) + p.f(p.grid(), sigma * p.tau)
+    v = np.sin(np.pi * p.grid())
+    out = {}
+    for kind in ("strang", "tchan"):
+        P = O.preconditioner_matrix(p, 0, kind)
+        lam_min = float(np.abs(np.linalg.eigvals(P)).min())
+        rq = float(v @ np.linalg.solve(P, A @ v) / (v @ v))
+        x, its, _ = O.pcgs(A, g, P, maxit=500)
+        np.testing.assert_allclose(x, np.linalg.solve(A, g), rtol=1e-9, atol=1e-12)
+        out[kind] = (lam_min, rq, its)
+    assert eta <= out["strang"][0] <= 1.2 * eta, out
+    assert out["tchan"][0] >= 100.0 * eta, out
+    assert 1.0 <= out["strang"][1] <= 3.0 and out["tchan"][1] <= 0.05, out
+    assert out["tchan"][2] >= 2 * out["strang"][2], out
