@@ -708,6 +708,29 @@ def run_native_batch(args, probs_all):
     b.get_all(uM.data_ptr())
     e2e_s = ranks.max(time.perf_counter() - t0)
     b.close()
+    single = None
+    if ranks.world == 1 and args.single_sample > 0:
+        # the same first instances marched one at a time through the single-instance ABI, against
+        # one batch of just those instances (device time of the marches, FP64 or mixed alike)
+        sample = probs[:args.single_sample]
+        ms_one = 0.0
+        for q in sample:
+            with P.Solver.from_problem(q, source="callback", preconditioner=precond,
+                                       precision=args.precision, maxit=args.maxit,
+                                       algorithm=args.algorithm, stream=stream.cuda_stream,
+                                       autotune=not args.no_autotune) as s1:
+                ms_one += s1.step(M)["device_ms"]
+        with P.Batch(sample, M, preconditioner=precond, precision=args.precision, maxit=args.maxit,
+                     stream=stream.cuda_stream, algorithm=args.algorithm,
+                     autotune=not args.no_autotune) as bs:
+            bs.step(M)
+            bs.reset()
+            ms_batch = bs.step(M)["device_ms"]
+        upd = sum(q.n for q in sample) * M
+        single = {"instances": len(sample), "one_at_a_time_updates_per_s": upd / (ms_one / 1e3),
+                  "batched_updates_per_s": upd / (ms_batch / 1e3), "batched_over_one_at_a_time":
+                  ms_one / ms_batch, "note": "the first instances of the batch, same precision and "
+                  "algorithm; device time of the marches"}
     if ranks.rank != 0:
         return
     ns = np.array([p.n for p in probs_all])
@@ -744,6 +767,7 @@ def run_native_batch(args, probs_all):
                               "applications_per_level": apps_per_level,
                               "note": "cgs_iterations include the two generator solves at level 1"}
                              if const else None),
+        "single_instance_sample": single,
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
@@ -1003,7 +1027,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="skip the setup-time FFT-plan tuner")
     ap.add_argument("--algorithm", default="ids", choices=["ids", "ids-const"],
                     help="batch workload: ids-const = constant-coefficient algorithm (Gohberg-Semencul)")
-    ap.add_argument("--co", action="store_true", help="history workload: also run M/2 for CO_tau")
+    ap.add_argument("--co", action="store_true",
+                    help="history workload: also march M/2 and M/4 levels for CO_tau")
+    ap.add_argument("--single-sample", type=int, default=32,
+                    help="batch workload: march this many of its instances one at a time through "
+                         "the single-instance ABI too, and as a batch of their own (0: skip)")
     args = ap.parse_args()
     global _ARGS
     _ARGS = args
