@@ -276,8 +276,8 @@ int tsfcde_apply(tsfcde_ctx *ctx, int32_t op, int64_t j, const double *x, double
  * All scratch (WSGD weights, twiddles, spectra, FFT work arrays, barrier words) lives in one
  * fixed 3 MiB file-scope device array that each device holds from library load until process
  * exit.  The first call on a device looks up that array's address and sets the kernel's
- * shared-memory limit; make that first call before any stream capture.  Every call reuses the
- * array: calls that overlap on the GPU race and must be serialised by the caller.  Returns
+ * shared-memory limit.  Every call reuses the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  Each call copies its status word to the host and returns
  * after the product is complete (it synchronises `stream`). */
 int tsfcde_apply_operator_static(int64_t N, double beta, double sigma, double eta, double q,
                                  double kappa_plus, double kappa_minus, int32_t op,
